@@ -1,0 +1,101 @@
+"""Pins of the oracle's geometry and Fried operator (Sect. 3, Sect. 2.3)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fried, geometry
+from synth.wfs import FineGridSensor
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("case", json.load(open(os.path.join(GOLDEN, "paper_counts.json")))["cases"])
+def test_valid_counts_match_paper(case):
+    g = geometry.make_geometry(case["n_sub"], case["obstruction"])
+    assert g.n_act == case["n_act"]
+    if "n_subv" in case:
+        assert g.n_subv == case["n_subv"]
+        assert g.n == case["n"]
+        assert g.p == case["p"]
+
+
+def test_mask_symmetry_and_annulus():
+    # the pupil is centred: the masks are invariant under the dihedral symmetries of the grid
+    for n, obs in [(16, 0.0), (40, 0.14), (80, 0.28)]:
+        s = geometry.subaperture_mask(n, obs)
+        assert np.array_equal(s, s[::-1, :]) and np.array_equal(s, s[:, ::-1]) and np.array_equal(s, s.T)
+        if obs > 0:
+            assert not s[n // 2, n // 2]      # the obstruction removes the centre
+
+
+def test_brute_force_area_rule():
+    # brute force on a tiny grid: exact area fraction by dense sampling agrees away from ties
+    n = 8
+    s = geometry.subaperture_mask(n, 0.0)
+    fine = 400
+    t = (np.arange(fine) + 0.5) / fine
+    for r in range(n):
+        for c in range(n):
+            x = c + t[None, :] - n / 2
+            y = r + t[:, None] - n / 2
+            frac = np.mean(x * x + y * y <= (n / 2) ** 2)
+            if abs(frac - 0.5) > 0.02:
+                assert s[r, c] == (frac >= 0.5)
+
+
+def test_domains_partition_actuators():
+    for n, obs, b, h in [(8, 0.0, 4, 1), (40, 0.14, 4, 2), (80, 0.28, 4, 2), (16, 0.0, 4, 2)]:
+        g = geometry.make_geometry(n, obs)
+        doms = geometry.make_domains(g, b, h)
+        owned = np.concatenate([d.owned_act for d in doms])
+        assert np.array_equal(np.sort(owned), np.arange(g.n_act))  # each actuator owned once
+        for d in doms:
+            assert d.owned_act.size > 0
+            # every observed subaperture lies in the block grown by the halo
+            rc = g.sub_rc[d.obs_sub]
+            assert np.all(rc[:, 0] >= b * d.I - h) and np.all(rc[:, 0] < b * (d.I + 1) + h)
+            assert np.all(rc[:, 1] >= b * d.J - h) and np.all(rc[:, 1] < b * (d.J + 1) + h)
+
+
+def test_tiny_domain_sizes():
+    g = geometry.make_geometry(8, 0.0)
+    doms = geometry.make_domains(g, 4, 1)
+    assert len(doms) == 4
+    assert all(d.obs_sub.size == 22 for d in doms)   # 44 slopes per domain
+
+
+def test_fried_closed_forms():
+    g = geometry.make_geometry(16, 0.0)
+    D = fried.fried_matrix(g)
+    r, c = g.act_rc[:, 0].astype(float), g.act_rc[:, 1].astype(float)
+    ns = g.n_subv
+    alpha, beta = 0.37, -1.25
+    s = D @ (alpha * c + beta * r)                    # tilt: slopes equal the tilt in every subaperture
+    assert np.allclose(s[:ns], alpha, atol=1e-12) and np.allclose(s[ns:], beta, atol=1e-12)
+    assert np.allclose(D @ np.ones(g.n_act), 0.0, atol=1e-12)          # piston is invisible
+    waffle = (-1.0) ** (g.act_rc[:, 0] + g.act_rc[:, 1])
+    assert np.allclose(D @ waffle, 0.0, atol=1e-12)                    # waffle is invisible
+    # a single poked actuator in the interior moves exactly four subapertures by +-1/2 in each direction
+    k = g.act_index[8, 8]
+    e = np.zeros(g.n_act)
+    e[k] = 1.0
+    sx, sy = (D @ e)[:ns], (D @ e)[ns:]
+    assert np.count_nonzero(sx) == 4 and np.allclose(np.sort(sx[sx != 0]), [-0.5, -0.5, 0.5, 0.5])
+    assert np.count_nonzero(sy) == 4 and np.allclose(np.sort(sy[sy != 0]), [-0.5, -0.5, 0.5, 0.5])
+
+
+def test_fried_matches_fine_sensor_at_one_sample_per_pitch():
+    # the generator's sensor is an independent code path; with q = 1 it is the corner difference
+    rng = np.random.default_rng(7)
+    n = 12
+    g = geometry.make_geometry(n, 0.1)
+    phi = rng.standard_normal((n + 1, n + 1))
+    sx, sy, pa = FineGridSensor(n, 1).measure(phi)
+    D = fried.fried_matrix(g)
+    s = D @ phi[g.act_valid]
+    assert np.allclose(s[: g.n_subv], sx[g.sub_valid], atol=1e-12)
+    assert np.allclose(s[g.n_subv:], sy[g.sub_valid], atol=1e-12)
+    assert np.array_equal(pa, phi)

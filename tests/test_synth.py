@@ -1,0 +1,67 @@
+"""Checks of the seeded input generators (turbulence statistics, sensor, workloads)."""
+
+import math
+
+import numpy as np
+from scipy import integrate, special
+
+from synth import TruthStream, VKScreen, vk_phase_covariance, vk_structure_function_kolmogorov, workload
+from synth.turbulence import vk_psd
+
+
+def test_vk_covariance_is_hankel_transform_of_psd():
+    r0, L0 = 0.5, 25.0
+    var = integrate.quad(lambda f: 2 * math.pi * f * vk_psd(f * f, r0, L0), 0, np.inf, limit=500)[0]
+    # 0.023 is the rounded PSD constant, so agreement is at the 1 % level
+    assert abs(vk_phase_covariance(np.array([0.0]), r0, L0)[0] / var - 1) < 0.01
+    c1 = integrate.quad(lambda f: 2 * math.pi * f * vk_psd(f * f, r0, L0) * special.j0(2 * math.pi * f),
+                        0, 50, limit=2000)[0]
+    assert abs(vk_phase_covariance(np.array([1.0]), r0, L0)[0] / c1 - 1) < 0.01
+
+
+def test_structure_function_kolmogorov_limit():
+    # r << L0: D(r) = 6.88 (r/r0)^(5/3) [1 - 1.485 (r/L0)^(1/3) + ...] (first outer-scale term)
+    for r0, L0 in [(0.3, 1e5), (0.5, 25.0)]:
+        r = np.array([0.01, 0.05, 0.2]) if L0 > 1e3 else np.array([0.001, 0.003, 0.01])
+        C0 = vk_phase_covariance(np.array([0.0]), r0, L0)[0]
+        Dr = 2 * (C0 - vk_phase_covariance(r, r0, L0))
+        ref = vk_structure_function_kolmogorov(r, r0) * (1 - 1.485 * (r / L0) ** (1 / 3))
+        assert np.allclose(Dr / ref, 1.0, rtol=2e-3)
+
+
+def test_fft_screen_structure_function():
+    r0, L0, dx = 0.5, 25.0, 0.125
+    scr = VKScreen(1024, dx, r0, L0, seed=4)
+    C0 = vk_phase_covariance(np.array([0.0]), r0, L0)[0]
+    for lag in (2, 4, 8, 32):   # lag 1 misses the power above the grid Nyquist frequency
+        emp = np.mean((scr.phase[:, lag:] - scr.phase[:, :-lag]) ** 2)
+        ref = 2 * (C0 - vk_phase_covariance(np.array([lag * dx]), r0, L0)[0])
+        assert abs(emp / ref - 1) < 0.1
+
+
+def test_process_noise_is_frozen_flow_innovation_covariance():
+    w = workload("tiny-8x8")
+    rc = np.array([(r, c) for r in range(3) for c in range(3)])
+    L = w.process_noise_sqrt(rc, jitter=0.0)
+    P = rc[:, ::-1] * w.pitch
+    s = np.array([w.wind / w.frame_rate, 0.0])
+    a = w.ar1_a
+    # brute force: Cov(phi_{k+1}(i) - a phi_k(i), phi_{k+1}(j) - a phi_k(j)), phi_{k+1}(x) = phi_k(x - s)
+    Q = np.zeros((9, 9))
+    for i in range(9):
+        for j in range(9):
+            c = lambda u, v: vk_phase_covariance(np.array([np.linalg.norm(u - v)]), w.r0, w.L0)[0]
+            Q[i, j] = (c(P[i] - s, P[j] - s) - a * c(P[i] - s, P[j]) - a * c(P[i], P[j] - s)
+                       + a * a * c(P[i], P[j]))
+    assert np.allclose(L @ L.T, Q, rtol=1e-8, atol=1e-12)
+
+
+def test_truth_stream_shapes_and_determinism():
+    w = workload("tiny-8x8")
+    a = TruthStream(w).frames(0, 3)
+    b = TruthStream(w).frames(0, 3)
+    assert a["slopes"].shape == (3, 2, 8, 8) and a["phi_act"].shape == (3, 9, 9)
+    assert np.array_equal(a["slopes"], b["slopes"]) and np.array_equal(a["phi_act"], b["phi_act"])
+    # frozen flow: consecutive frames differ by a small shift of the same screen
+    d = np.std(a["phi_act"][1] - a["phi_act"][0])
+    assert 0 < d < 0.5 * np.std(a["phi_act"][0])
