@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the local ETKF frame update on GB300.
+
+One step = one filter frame of the whole hot path (slope check, process-noise draw,
+observed anomalies, local Gram / eigensolve / weights per domain, transform,
+AR(1) forecast, x_hat(k+1|k) output) for the ELT-class workload: 80 x 80
+subapertures, 28 % obstruction, m = 100 members, 332 domains of 4 x 4
+subapertures with a 2-subaperture halo.  Inputs are seeded synthetic von Karman
+frozen-flow frames (see synth/).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same
+workload instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LETKF frames/s and p99 frame latency, tuned vs plain, at matched residual RMS"
+FP32_ALU_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="elt-80x80")
+    ap.add_argument("--path", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp32", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-path comparison run")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=256)
+    ap.add_argument("--profile-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        under = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(under), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_inputs(wname, n_frames, sub_valid, act_valid):
+    """Seeded truth frames compressed with the filter's own geometry (valid subapertures/actuators)."""
+    from synth import TruthStream, workload
+    w = workload(wname)
+    fr = TruthStream(w).frames(0, n_frames + 1)
+    y = np.concatenate([fr["slopes"][:, 0][:, sub_valid], fr["slopes"][:, 1][:, sub_valid]], axis=1)
+    phi = fr["phi_act"][:, act_valid]
+    return w, y, phi
+
+
+def residual_rms(xpred, phi, burn):
+    """sqrt of the mean over frames >= burn of ||phi_true(k+1) - x_hat(k+1|k)||^2 / n_act, piston removed."""
+    e = phi[1:len(xpred) + 1] - xpred
+    e = e - e.mean(axis=1, keepdims=True)
+    e = e[burn:]
+    return float(math.sqrt(np.mean(np.sum(e * e, axis=1) / e.shape[1])))
+
+
+def make_filter(w, path, precision, L, Ls, seed_offset=0):
+    from paper_1310_5954_gb300 import LETKF
+    return LETKF(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
+                 obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=precision, path=path,
+                 seed=w.seed + seed_offset, obs_block=w.obs_block)
+
+
+def run_device(f, y_dev, K, W, flush, torch):
+    """W warm-up steps, then K timed steps, each bracketed by CUDA events on the filter's stream,
+    with L2 flushed (a write larger than L2) before each timed step.  Returns per-step ms and all
+    predictions (W + K, n_act) on the host."""
+    st = f.stream
+    preds = torch.empty((W + K, f.info.n_act), dtype=f.dtype, device=f.device)
+    for k in range(W):
+        f.step(y_dev[k], out=preds[k])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(st):
+        for k in range(K):
+            flush.fill_(float(k & 7))
+            ev[k][0].record(st)
+            f.step(y_dev[W + k], out=preds[W + k])
+            ev[k][1].record(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, preds.double().cpu().numpy(), wall
+
+
+def run_e2e(f, y_host, K, W, torch):
+    """Through the public API with host buffers: per frame, pinned host -> device copy of the
+    slopes, the step, and a device -> host read of x_hat(k+1|k); the frame is complete when
+    the prediction is on the host."""
+    st = f.stream
+    p = f.info.p
+    y_dev = torch.empty(p, dtype=f.dtype, device=f.device)
+    out_dev = torch.empty(f.info.n_act, dtype=f.dtype, device=f.device)
+    out_host = torch.empty(f.info.n_act, dtype=f.dtype, pin_memory=True)
+    lat = []
+    with torch.cuda.stream(st):
+        for k in range(W):
+            y_dev.copy_(y_host[k], non_blocking=True)
+            f.step(y_dev, out=out_dev)
+            out_host.copy_(out_dev, non_blocking=True)
+            st.synchronize()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            t = time.perf_counter()
+            y_dev.copy_(y_host[W + k], non_blocking=True)
+            f.step(y_dev, out=out_dev)
+            out_host.copy_(out_dev, non_blocking=True)
+            st.synchronize()
+            lat.append((time.perf_counter() - t) * 1e3)
+        wall = time.perf_counter() - t0
+    return K / wall, lat, p * y_dev.element_size(), f.info.n_act * out_dev.element_size()
+
+
+def stage_profile(f, y_dev, steps, flush, torch):
+    f.profile(True)
+    with torch.cuda.stream(f.stream):
+        for k in range(steps):
+            flush.fill_(float(k & 7))
+            f.step(y_dev[k % y_dev.shape[0]])
+    return f.profile(False)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def roofline(f, w, prof, sms, sm_max_mhz):
+    """Dominant stage: the one with the largest total event time.  Its algorithmic work per launch:
+    eigensolve stage (plain) and fused kernel: 11 m^3 FP32 flops per observing domain (an
+    eigendecomposition with vectors plus the transform, the dense-eigensolver count), bound by the
+    FP32 ALUs; every other stage is counted by its algorithmic bytes against HBM."""
+    name, (ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = ms / max(launches, 1)
+    m = f.info.m
+    n_obs_dom = f.info.n_domains
+    if name in ("eigensolve_weights", "fused_analysis_forecast"):
+        flops = 11.0 * m ** 3 * n_obs_dom
+        peak = sms * FP32_ALU_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "per_launch_ms": per_launch_ms,
+                "work_per_launch": flops, "peak_source": f"{sms} SMs x {FP32_ALU_LANES_PER_SM} FP32 lanes x 2 "
+                                                         f"x {sm_max_mhz:.0f} MHz (derived)"}
+    bytes_ = 8.0 * f.info.n * m * (2 if f.precision == "fp64" else 1)
+    pk = peaks().get("hbm_gbs", 6800.0)
+    achieved = bytes_ / (per_launch_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
+            "frac": achieved / pk, "traffic": None, "per_launch_ms": per_launch_ms, "work_per_launch": bytes_,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
+def cpu_baseline(wname, y, seconds, L, Ls):
+    """The FP64 oracle as it stands, on this host's cores, over the first frames of the workload."""
+    from oracle import etkf, geometry
+    from synth import workload
+    w = workload(wname)
+    g = geometry.make_geometry(w.n_sub, w.obstruction)
+    doms = geometry.make_domains(g, w.dom_sub, w.halo)
+    o = etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls)
+    preds = []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and len(preds) < len(y):
+        preds.append(o.step(y[len(preds)]))
+    dt = time.perf_counter() - t0
+    return len(preds) / dt, np.array(preds), len(preds), dt
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_main(args, world, rank)
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1310_5954_gb300 import LETKF  # noqa: F401
+    from synth import workload
+    precision = args.precision or ("mixed" if args.path == "fused" else "fp32")
+    w = workload(args.workload)
+    K, W = args.steps, args.warmup
+    # geometry from the library itself (what the filter will use)
+    probe = LETKF(n_sub=w.n_sub, m=4, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
+                  obstruction=w.obstruction, q_white=0.1, precision="fp32", path="plain")
+    sub_valid, act_valid = probe.geometry()
+    probe.close()
+    act_rc = np.argwhere(act_valid)
+    L = w.process_noise_sqrt(act_rc)
+    Ls = w.stationary_sqrt(act_rc)
+    w, y, phi = workload_inputs(args.workload, W + K, sub_valid, act_valid)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
+
+    def timed(path, prec, seed_offset):
+        f = make_filter(w, path, prec, L, Ls, seed_offset)
+        ydev = torch.as_tensor(y, dtype=f.dtype, device=dev).contiguous()
+        if world > 1:
+            dist.barrier()
+        ms, preds, wall = run_device(f, ydev, K, W, flush, torch)
+        prof = stage_profile(f, ydev, args.profile_steps, flush, torch)
+        status = f.sync()
+        return f, ms, preds, wall, prof, ydev, status
+
+    clocks = Clocks(local)
+    f, ms, preds, wall, prof, ydev, status = timed(args.path, precision, rank)
+    clk = clocks.stop()
+    tot = sum(ms) / 1e3
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    value = world * K / tot
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    roof = roofline(f, w, prof, torch.cuda.get_device_properties(dev).multi_processor_count, sm_max)
+    # end to end through the public API, host buffers
+    y_host = torch.as_tensor(y, dtype=f.dtype).pin_memory()
+    fe = make_filter(w, args.path, precision, L, Ls, rank)
+    e2e_fps, e2e_lat, h2d, d2h = run_e2e(fe, y_host, K, W, torch)
+    fe.close()
+    burn = min(50, (W + K) // 4)
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * tot / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "bf16+f32", "fp32": "f32", "fp64": "f64"}[precision], "data": "synthetic",
+        "impl": "gpu",
+        "config": {"workload": f"{w.name}: {w.n_sub}x{w.n_sub} subapertures, {int(w.obstruction * 100)}% "
+                               f"obstruction, m={w.m}, {f.info.n_domains} domains {w.dom_sub}x{w.dom_sub}+halo "
+                               f"{w.halo}, n={f.info.n}, p={f.info.p}",
+                   "path": args.path, "precision": precision,
+                   "l2": f"flushed before every timed step ({args.flush_mb} MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "roofline": roof, "gpu_launches": int(K * sum(v[1] for v in prof.values()) / max(args.profile_steps, 1)),
+        "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items()},
+        "clocks": clk, "device_status": status,
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "p50_ms": float(np.percentile(e2e_lat, 50)), "p99_ms": float(np.percentile(e2e_lat, 99))},
+        "residual_rms": {"frames": W + K, "burn_in": burn, args.path: residual_rms(preds, phi, burn)},
+    }
+    f.close()
+    if world == 1 and not args.no_compare:
+        other = "plain" if args.path == "fused" else None
+        if other:
+            fp, msp, predp, _, profp, _, stp = timed(other, "fp32", 0)
+            out["plain"] = {"value": K / (sum(msp) / 1e3), "ms_per_step": sum(msp) / K,
+                            "p50_ms": float(np.percentile(msp, 50)), "p99_ms": float(np.percentile(msp, 99)),
+                            "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in profp.items()},
+                            "device_status": stp}
+            out["residual_rms"]["plain"] = residual_rms(predp, phi, burn)
+            out["speedup_vs_plain"] = out["value"] / out["plain"]["value"]
+            fp.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fps, opreds, nfr, dt = cpu_baseline(args.workload, y, args.cpu_seconds, L, Ls)
+        out["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"first {nfr} frames of {w.name}, FP64 numpy/LAPACK oracle, {dt:.1f} s"}
+        nb = min(burn, max(nfr - 2, 0))
+        out["residual_rms"]["oracle_first_frames"] = {"frames": nfr, "burn_in": nb,
+                                                      "oracle": residual_rms(opreds, phi, nb),
+                                                      args.path: residual_rms(preds[:nfr], phi, nb)}
+        if "plain" in out:
+            out["residual_rms"]["oracle_first_frames"]["plain"] = residual_rms(predp[:nfr], phi, nb)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference_main(args, world, rank):
+    """The oracle as it stands on the host cores (rank 0 only): W + K frames of the same workload,
+    each frame one step, stopped early after a bounded time budget."""
+    if rank != 0:
+        return
+    from oracle import geometry
+    from synth import workload
+    w = workload(args.workload)
+    g = geometry.make_geometry(w.n_sub, w.obstruction)
+    L = w.process_noise_sqrt(g.act_rc)
+    Ls = w.stationary_sqrt(g.act_rc)
+    _, y, _ = workload_inputs(args.workload, args.warmup + args.steps, g.sub_valid, g.act_valid)
+    from oracle import etkf
+    doms = geometry.make_domains(g, w.dom_sub, w.halo)
+    o = etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls)
+    for k in range(args.warmup):
+        o.step(y[k])
+    budget = 150.0
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        o.step(y[args.warmup + k])
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    fps = done / dt
+    out = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": done,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / done, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{w.name}: {w.n_sub}x{w.n_sub} subapertures, m={w.m}, {len(doms)} domains",
+                      "path": "oracle"},
+           "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{done} frames after {args.warmup} warm-up frames"
+                                      + (" (stopped at the time budget)" if done < args.steps else "")},
+           "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * letkf.h - C ABI of the GB300 local ETKF control law (arXiv:1310.5954).
+ *
+ * One context = one adaptive-optics system: its geometry, its filter model and
+ * its ensemble, all resident on one GPU.  The filter is the local ensemble
+ * transform Kalman filter of Sect. 2.3: every frame, each estimation domain
+ * runs an independent ensemble-transform analysis against the slopes of its
+ * observation region, then every member is propagated by the AR(1) model of
+ * Sect. 2.1.
+ *
+ * Model (Sect. 2.1, Sect. 3):
+ *   state     x = [phi_k ; phi_{k-1}] on the valid actuators (Fried geometry),
+ *             n = 2 * n_act, rows: all actuators of the first instant, then the
+ *             second, valid actuators numbered in row-major grid order;
+ *   dynamics  x_{k+1} = A1 x_k + [v_k ; 0],  A1 = [[a I, 0], [I, 0]],  v ~ N(0, Q);
+ *   slopes    y_k = C x_k + w_k,  C = [0 D] (obs_block = 1) or [D 0] (obs_block = 0),
+ *             D the Fried difference operator, p = 2 * n_subv, all x-slopes then
+ *             all y-slopes of the valid subapertures in row-major grid order;
+ *             R = sigma^2 I.
+ * Update (ETKF with symmetric square root, Sect. 2.2, refs. [8-10], [14]):
+ *   G = Y'^T R^-1 Y',  w_bar = [(m-1)I + G]^-1 Y'^T R^-1 (y - y_bar),
+ *   T = sqrt(m-1) [(m-1)I + G]^(-1/2),  X_a = x_bar 1^T + X' (w_bar 1^T + T),
+ * per domain, on the domain's own actuators (both instants) with the slopes
+ * of its observation region.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a letkf_status and never throws or aborts.
+ *   - Device buffers are plain device pointers owned by the caller; the
+ *     library reads or writes them in stream order on the context's stream and
+ *     never keeps them after the call's work completes.
+ *   - Element type of every device buffer ("state type"): double when the
+ *     context's precision is LETKF_PREC_FP64, float otherwise.  Matrices are
+ *     row-major with no padding: an (r x m) buffer holds element (i, j) at i*m + j.
+ *   - Work is asynchronous.  Errors detected on the device (non-finite input,
+ *     a bounded wait that ran out, an eigensolver that did not converge) are
+ *     latched in the context and reported by letkf_sync (and by the next
+ *     letkf_sync only: reading clears them).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef LETKF_H
+#define LETKF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct letkf_ctx letkf_ctx;
+
+typedef enum letkf_status {
+    LETKF_OK = 0,
+    LETKF_EINVAL = -1,      /* invalid argument or unsupported configuration */
+    LETKF_ENOMEM = -2,      /* device or host allocation failed */
+    LETKF_ECUDA = -3,       /* a CUDA runtime or cuBLAS call failed */
+    LETKF_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
+    LETKF_ENONFINITE = -5,  /* non-finite slopes: that frame was rejected, state unchanged */
+    LETKF_ESTATE = -6,      /* call out of order (e.g. analyze twice without a forecast) */
+    LETKF_ENOCONV = -7      /* a domain eigensolve hit its sweep limit (result still written) */
+} letkf_status;
+
+typedef enum letkf_precision {
+    LETKF_PREC_FP64 = 0,    /* everything in FP64 (plain path only) */
+    LETKF_PREC_FP32 = 1,    /* everything in FP32 */
+    LETKF_PREC_MIXED = 2    /* BF16 tensor-core products with FP32 accumulation, FP32 eigensolve,
+                               FP64 eigenvalue functions and mean-weight sums (fused path only) */
+} letkf_precision;
+
+typedef enum letkf_path {
+    LETKF_PATH_PLAIN = 0,   /* one kernel per stage, one CTA per domain */
+    LETKF_PATH_FUSED = 1    /* one persistent kernel per frame over all domains */
+} letkf_path;
+
+typedef struct letkf_params {
+    int n_sub;                      /* N: subapertures across; (N+1)^2 actuator grid (Fried) */
+    const unsigned char* sub_valid; /* host N*N row-major validity mask, or NULL: circular pupil
+                                       rule (a subaperture is valid when >= half of its area,
+                                       sampled on a 20x20 midpoint grid, lies in the annulus
+                                       [obstruction*N/2, N/2] pitches around the grid centre) */
+    double obstruction;             /* central obstruction ratio, used when sub_valid is NULL */
+    double ar1_a;                   /* AR(1) coefficient a of A1, |a| < 1 */
+    int obs_block;                  /* 1: slopes see the second instant (C = [0 D]); 0: the first */
+    const double* q_sqrt;           /* host n_act*n_act row-major L with Q = L L^T (lower
+                                       triangular or dense), or NULL for white noise q_white */
+    double q_white;                 /* process-noise std when q_sqrt is NULL */
+    const double* p0_sqrt;          /* host n_act*n_act factor of the stationary covariance of
+                                       one phase instant, for the initial ensemble; NULL means
+                                       L / sqrt(1 - a^2) */
+    double sigma;                   /* slope-noise std: R = sigma^2 I */
+    int m;                          /* ensemble size, 2 <= m <= 256 (plain FP64: <= 112,
+                                       plain FP32: <= 160) */
+    int dom_sub;                    /* estimation-domain side in subapertures (>= 1) */
+    int halo;                       /* observation halo in subapertures (>= 0) */
+    int precision;                  /* letkf_precision */
+    int path;                       /* letkf_path */
+    unsigned long long seed;        /* key of the Philox4x32-10 draws (initial ensemble,
+                                       process noise) */
+    int device;                     /* CUDA device ordinal */
+    void* stream;                   /* cudaStream_t borrowed from the caller (NULL: default) */
+} letkf_params;
+
+typedef struct letkf_info {
+    int n_sub, n_act, n_subv, n, p, m;
+    int n_domains;
+    int n_loc_max;                  /* largest number of state rows a domain updates */
+    int p_loc_max;                  /* largest number of slopes a domain observes */
+    int rank_max;                   /* largest rank of a domain's observation operator */
+    int state_bytes;                /* 8 (FP64) or 4 */
+    int precision, path;
+    unsigned long long frame;       /* frames forecast so far */
+    size_t device_bytes;            /* device memory held by the context */
+} letkf_info;
+
+/*
+ * letkf_create: build the geometry (Sect. 3: Fried actuators on the corners
+ * of the valid subapertures), the domain decomposition (Sect. 2.3: dom_sub x
+ * dom_sub blocks of subapertures own their actuators; the observation region is
+ * the block grown by `halo` subapertures), the device tables, and the initial
+ * ensemble (Sect. 2.2): second instant = P0 xi0, first instant = a * second + L xi1,
+ * with xi0, xi1 Philox normals (stream 0, frames 0 and 1).  The new context is
+ * in the forecast phase at frame 0.  *out is set to NULL on failure.
+ */
+int letkf_create(const letkf_params* params, letkf_ctx** out);
+
+/* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
+int letkf_destroy(letkf_ctx* ctx);
+
+int letkf_get_info(const letkf_ctx* ctx, letkf_info* out);
+
+/* Host copies of the validity masks: sub_valid N*N, act_valid (N+1)*(N+1); either may be NULL. */
+int letkf_get_geometry(const letkf_ctx* ctx, unsigned char* sub_valid, unsigned char* act_valid);
+
+/*
+ * letkf_analyze: local ETKF analysis (Sect. 2.3) of the current forecast
+ * ensemble with slopes y_dev (p elements, state type).  sigma > 0 replaces the
+ * noise std from this frame on; sigma <= 0 keeps it.  Requires the forecast
+ * phase (else LETKF_ESTATE); leaves the context in the analysis phase.  A frame
+ * with a non-finite slope is rejected on the device: the ensemble is left
+ * unchanged, the following letkf_forecast is skipped as well, and letkf_sync
+ * reports LETKF_ENONFINITE.
+ */
+int letkf_analyze(letkf_ctx* ctx, const void* y_dev, double sigma);
+
+/*
+ * letkf_forecast: AR(1) forecast of every member (Sect. 2.1): first instant
+ * <- a * first + v, second instant <- first.  v_dev: n_act x m perturbations
+ * (state type), or NULL to draw v = L xi with xi Philox normals (stream 1, frame
+ * = the context's frame counter).  Advances the frame counter.  Allowed in both
+ * phases (a forecast without analysis is a prediction with no data).
+ */
+int letkf_forecast(letkf_ctx* ctx, const void* v_dev);
+
+/*
+ * letkf_step: one filter frame in the prediction form of Eq. 1: analysis with
+ * y_k, then forecast with internally drawn noise; writes x_hat(k+1|k), the
+ * ensemble mean of the first instant (n_act elements, state type), to xpred_dev
+ * (may be NULL).  Requires the forecast phase.
+ */
+int letkf_step(letkf_ctx* ctx, const void* y_dev, double sigma, void* xpred_dev);
+
+/* Ensemble as an n x m matrix (state type) and the frame counter (either may be NULL). */
+int letkf_get_state(letkf_ctx* ctx, void* x_dev, unsigned long long* frame);
+
+/* Replace the ensemble (n x m, state type) and frame counter; puts the context in the forecast
+ * phase.  With letkf_get_state this checkpoints and resumes a filter bit for bit. */
+int letkf_set_state(letkf_ctx* ctx, const void* x_dev, unsigned long long frame);
+
+/* Wait for the context's queued work and return the first latched device error, clearing it. */
+int letkf_sync(letkf_ctx* ctx);
+
+/* Static English description of a status code. */
+const char* letkf_status_string(int status);
+
+/*
+ * Stage timing (instrumentation; the paper has no counterpart).  Stages:
+ * 0 slope check, 1 process-noise draw (normals + GEMM), 2 observed anomalies,
+ * 3 Gram, 4 eigensolve and weights, 5 transform, 6 forecast, 7 fused
+ * analysis+forecast.  letkf_profile(ctx, 1, NULL) starts recording a pair of
+ * CUDA events around every stage launched on the context's stream (previous
+ * records are dropped); letkf_profile(ctx, 0, out) stops, waits for the recorded
+ * work and writes, per stage, the summed event time in milliseconds and the
+ * number of launches.  Recording adds two event records per launch.
+ */
+#define LETKF_N_STAGES 8
+typedef struct letkf_stage_times {
+    double ms[LETKF_N_STAGES];
+    int launches[LETKF_N_STAGES];
+} letkf_stage_times;
+
+int letkf_profile(letkf_ctx* ctx, int enable, letkf_stage_times* out);
+
+/* Static name of a stage index (0 .. LETKF_N_STAGES-1), or "unknown". */
+const char* letkf_stage_name(int stage);
+
+/*
+ * Self-test of the tensor-core product used by the fused path (diagnostic; the paper has no
+ * counterpart).  D (128 x n) = A (128 x k) * op(B), FP32 row-major device buffers owned by the
+ * caller: b_layout = 0 gives B as n x k and op(B) = B^T; b_layout = 1 gives B as k x n and
+ * op(B) = B.  16 <= n <= 256 and 16 <= k <= 128, both multiples of 16.  The operands are
+ * rounded to BF16 (terms = 1) or split into BF16 high and low parts whose three cross products
+ * are accumulated (terms = 3), with FP32 accumulation in tensor memory.  Runs one CTA on
+ * `stream` (cudaStream_t, NULL: default) and synchronises it.  Returns LETKF_EINVAL for other
+ * arguments, LETKF_ETIMEOUT if the completion wait ran out.
+ */
+int letkf_umma_selftest(const float* a_dev, const float* b_dev, float* d_dev, int n, int k, int terms,
+                        int b_layout, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LETKF_H */

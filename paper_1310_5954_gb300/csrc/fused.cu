@@ -1,0 +1,803 @@
+// Fused per-frame local ETKF kernel on the tensor cores (Sect. 2.3 analysis + Sect. 2.1 forecast).
+//
+// One persistent CTA per SM takes domains from a work queue (most expensive first).  Per
+// domain, every product runs as a 128-row tcgen05 BF16 MMA with FP32 accumulation in
+// tensor memory:
+//
+//   1. stage the domain's halo rows (observed instant) and own rows with 1-D bulk copies;
+//   2. Fried slopes of the halo anomalies, S = Y'/sigma, with the innovation d/sigma
+//      appended as one more row, written as BF16 operands; G_aug = S_aug^T S_aug gives
+//      G = Y'^T R^-1 Y' and, in its extra column, b = Y'^T R^-1 d (the local Gram, a3);
+//   3. T = sqrt(m-1) [(m-1)I + G]^(-1/2) = (I + G/(m-1))^(-1/2) by the coupled
+//      Newton-Schulz iteration on A_s = (I + G/(m-1))/s, s = 1 + ||G||_F/(m-1):
+//        P = Z Y,  T_k = (3I - P)/2,  Y <- Y T_k,  Z <- T_k Z,   Z -> A_s^(-1/2)
+//      (matrix inverse square root by matrix products only; operands split into BF16
+//      high and low parts, three products per step, which holds FP32-level accuracy);
+//   4. mean weights w_bar = [(m-1)I + G]^-1 b = Z (Z b) / ((m-1) s), refined once with the
+//      residual b - ((m-1)I + G) w_bar summed in FP64;
+//   5. X_a[E] = x_bar[E] 1^T + X'[E] (T + w_bar 1^T) as one more MMA, whose epilogue applies
+//      the AR(1) forecast (first instant <- a x_a + v, second <- x_a) and writes x_hat(k+1|k).
+//
+// Precision LETKF_PREC_MIXED uses single BF16 operands for the Gram and the transform;
+// LETKF_PREC_FP32 uses the three-product split everywhere.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.hpp"
+#include "umma.cuh"
+
+namespace letkf {
+namespace {
+
+using namespace umma;
+
+constexpr int FT = 256;                  // threads per CTA
+constexpr int MT = 128;                  // MMA rows
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
+constexpr int TM_G = 0, TM_P = 128, TM_Y = 256, TM_Z = 384, TM_COLS = 512;
+
+struct Ctrl {
+    uint64_t bar_load;
+    uint64_t bar_mma;
+    uint32_t tmem_base;
+    int item;
+    int abort;
+    int flag;
+    float s;
+    float rn;
+    float red[FT / 32];
+    double redd[FT / 32];
+};
+
+struct FusedArgs {
+    const float* X;
+    float* Xo;
+    const float* y;
+    const float* V;
+    float* xpred;
+    DomainTables tab;
+    int* status;
+    const int* frame_bad;
+    int* queue;
+    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP;
+    float inv_sigma, a, q_white;
+    int vmode, with_forecast, gram_terms, tr_terms, max_it;
+    float s_split;       // mixed precision: conditioning bound above which the Gram is split
+    unsigned long long seed;
+    uint32_t frame;
+    // shared-memory layout (bytes from the dynamic base)
+    int off_vec, off_xe, off_big, off_opg, sz_op, sz_opg;
+};
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Write 8 consecutive K-values of row `row` into the hi (and optionally lo) operand.
+__device__ __forceinline__ void store8(unsigned char* hi_base, unsigned char* lo_base, int row, int k0, int K,
+                                       const float (&v)[8], bool with_lo) {
+    __align__(16) __nv_bfloat16 h[8];
+    __align__(16) __nv_bfloat16 l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) split_bf16(v[u], h[u], l[u]);
+    const uint32_t off = op_offset(row, k0, K);
+    *reinterpret_cast<uint4*>(hi_base + off) = *reinterpret_cast<const uint4*>(h);
+    if (with_lo) *reinterpret_cast<uint4*>(lo_base + off) = *reinterpret_cast<const uint4*>(l);
+}
+
+// Issue D = sum over terms of X_t * op(W_t) on a (MT x N) tile with K columns (no commit).
+// X is K-major (MT rows x K).  w_mn = 0: W holds N rows x K columns and op(W) = W^T;
+// w_mn = 1: W holds K rows x N columns and op(W) = W (the true product).
+// terms: (Xh, Wh), (Xh, Wl), (Xl, Wh) - the first `nterms` of them.
+__device__ __forceinline__ void issue_product(uint32_t d_tmem, const unsigned char* xh, const unsigned char* xl,
+                                              const unsigned char* wh, const unsigned char* wl, int K, int N,
+                                              int nterms, int w_mn, int first_term = 0) {
+    const uint32_t idesc = idesc_bf16(MT, N, w_mn);
+    const uint32_t x_sbo = (uint32_t)(K >> 3) * 128u;
+    const uint32_t w_lbo = w_mn ? (uint32_t)(N >> 3) * 128u : 128u;
+    const uint32_t w_sbo = w_mn ? 128u : x_sbo;
+    const uint32_t w_step = 2u * w_lbo;
+    const unsigned char* xs[3] = {xh, xh, xl};
+    const unsigned char* ws[3] = {wh, wl, wh};
+    uint32_t acc = first_term > 0 ? 1u : 0u;
+    for (int t = first_term; t < nterms; ++t) {
+        const uint32_t xa = smem_u32(xs[t]), wa = smem_u32(ws[t]);
+        for (int ks = 0; ks < (K >> 4); ++ks) {
+            mma_bf16(d_tmem, sdesc(xa + ks * 256u, 128u, x_sbo), sdesc(wa + ks * w_step, w_lbo, w_sbo), idesc, acc);
+            acc = 1;
+        }
+    }
+}
+
+// Thread 0 waits for the phase with a time limit, then everyone acquires it.  Returns false
+// (and latches ST_TIMEOUT) if the limit ran out.
+__device__ bool wait_all(Ctrl* ctl, uint64_t* bar, uint32_t parity, int* status) {
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait_bounded(bar, parity, WAIT_CYCLES);
+        if (!ok) {
+            atomicOr(status, ST_TIMEOUT);
+            ctl->abort = 1;
+        }
+    }
+    __syncthreads();
+    if (ctl->abort) return false;
+    while (!mbar_try_wait(bar, parity)) {
+    }
+    return true;
+}
+
+__device__ __forceinline__ float block_sum(Ctrl* ctl, float v) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) ctl->red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < FT / 32; ++w) s += ctl->red[w];
+    __syncthreads();
+    return s;
+}
+
+// Domains that take no analysis (rejected frame, or no observation): rows copied exactly, and
+// the forecast applied unless the frame was rejected.
+__device__ void simt_rows(const FusedArgs& A, int e0, int n_own, bool rejected) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = warp; e < n_own; e += FT / 32) {
+        const int j = A.tab.own[e0 + e];
+        const float* x1 = A.X + (size_t)j * A.m_pad;
+        const float* x2 = A.X + (size_t)(A.n_act + j) * A.m_pad;
+        float* o1 = A.Xo + (size_t)j * A.m_pad;
+        float* o2 = A.Xo + (size_t)(A.n_act + j) * A.m_pad;
+        float s = 0.f;
+        for (int i = lane; i < A.m; i += 32) {
+            const float a1 = x1[i];
+            float n1 = a1;
+            if (rejected || !A.with_forecast) {
+                o1[i] = a1;
+                o2[i] = x2[i];
+            } else {
+                float v = 0.f;
+                if (A.vmode == 0) {
+                    v = A.V[(size_t)j * A.m_pad + i];
+                } else if (A.vmode == 1) {
+                    float z[4];
+                    normals4<float>(A.seed, 1u, A.frame, (uint32_t)i, (uint32_t)(j >> 2), z);
+                    v = A.q_white * z[j & 3];
+                }
+                n1 = A.a * a1 + v;
+                o1[i] = n1;
+                o2[i] = a1;
+            }
+            s += n1;
+        }
+        s = warp_sum(s);
+        if (A.xpred && lane == 0) A.xpred[j] = s / (float)A.m;
+    }
+}
+
+__global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Ctrl* ctl = reinterpret_cast<Ctrl*>(smem);
+    float* vec = reinterpret_cast<float*>(smem + A.off_vec);
+    float* xh_mean = vec;            // 256 (halo actuators)
+    float* xe_mean = vec + 256;      // 128 (own rows)
+    float* bvec = vec + 384;         // 128
+    float* wbar = vec + 512;         // 128
+    float* vtmp = vec + 640;         // 2 x 128 (column-half partial sums)
+    float* vv = vec + 896;           // 128
+    float* vr = vec + 1024;          // 128
+    float* uvec = vec + 1152;        // 128 (mean update of each own row)
+    float* dtv = vec + 1280;         // 128 (innovation d / sigma of each observed slope)
+    float* tvv = vec + 1408;         // 128 (slope-space residual)
+    double* dtmp = reinterpret_cast<double*>(vec + 1536);  // 2 x 128 doubles
+    float* XE = reinterpret_cast<float*>(smem + A.off_xe);
+    unsigned char* big = smem + A.off_big;
+    float* Xh = reinterpret_cast<float*>(big);
+    unsigned char* opg_h = big + A.off_opg;
+    unsigned char* opg_l = opg_h + A.sz_opg;
+    unsigned char* Yh = big;
+    unsigned char* Yl = big + A.sz_op;
+    unsigned char* Zh = big + 2 * A.sz_op;
+    unsigned char* Zl = big + 3 * A.sz_op;
+    unsigned char* Th = big + 4 * A.sz_op;
+    unsigned char* Tl = big + 5 * A.sz_op;
+    unsigned char* Ah = big;                 // transform operands reuse the NS region
+    unsigned char* Al = big + A.sz_op;
+    unsigned char* Bh = big + 2 * A.sz_op;
+    unsigned char* Bl = big + 3 * A.sz_op;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = 32 * (warp & 3) + lane;          // TMEM lane / matrix row of this thread
+    const int hh = warp >> 2;                        // column half of this thread
+    const int m = A.m, NP = A.NP, KP = A.KP, half = NP / 2;
+    const float c = (float)(m - 1);
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+
+    if (tid == 0) {
+        mbar_init(&ctl->bar_load, 1);
+        mbar_init(&ctl->bar_mma, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&ctl->tmem_base, TM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ctl->tmem_base;
+    const uint32_t tl = tbase + lane_off;
+    uint32_t ph_load = 0, ph_mma = 0;
+    const bool rejected = *A.frame_bad != 0;
+
+    for (;;) {
+        if (tid == 0) ctl->item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int item = ctl->item;
+        if (item >= A.n_dom || ctl->abort) break;
+        const int d = A.tab.order[item];
+        const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
+        const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
+        const int o0 = A.tab.obs_off[d], n_obs = A.tab.obs_off[d + 1] - o0;
+        const int p_loc = 2 * n_obs;
+        const int n_e = A.with_forecast ? n_own : 2 * n_own;
+        if (rejected || n_obs == 0) {
+            simt_rows(A, e0, n_own, rejected);
+            __syncthreads();
+            continue;
+        }
+        // ---- 1. stage the halo rows of the observed instant and the domain's own rows
+        if (tid == 0) {
+            const uint32_t rb = (uint32_t)A.m_pad * 4u;
+            mbar_arrive_expect_tx(&ctl->bar_load, rb * (uint32_t)(n_h + n_e));
+            for (int j = 0; j < n_h; ++j)
+                bulk_g2s(Xh + (size_t)j * A.m_pad, A.X + (size_t)(A.row_obs + A.tab.halo[h0 + j]) * A.m_pad, rb,
+                         &ctl->bar_load);
+            for (int e = 0; e < n_e; ++e) {
+                const int r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
+                bulk_g2s(XE + (size_t)e * A.m_pad, A.X + (size_t)r * A.m_pad, rb, &ctl->bar_load);
+            }
+        }
+        if (!wait_all(ctl, &ctl->bar_load, ph_load, A.status)) break;
+        ph_load ^= 1;
+        // ---- 2. halo anomalies, slopes and innovation as the Gram operand
+        for (int j = warp; j < n_h; j += FT / 32) {
+            float s = 0.f;
+            for (int i = lane; i < m; i += 32) s += Xh[(size_t)j * A.m_pad + i];
+            s = warp_sum(s);
+            const float mu = s / (float)m;
+            for (int i = lane; i < m; i += 32) Xh[(size_t)j * A.m_pad + i] -= mu;
+            if (lane == 0) xh_mean[j] = mu;
+        }
+        __syncthreads();
+        for (int t = tid; t < MT * (KP >> 3); t += FT) {
+            const int i = t % MT, kc = t / MT;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = kc * 8 + u;
+                float val = 0.f;
+                if (i <= m && k < p_loc) {
+                    const int dir = k < n_obs ? 0 : 1;
+                    const int s = k - dir * n_obs;
+                    const int pc = A.tab.obs_corner[o0 + s];
+                    const int c00 = pc & 0xFF, c01 = (pc >> 8) & 0xFF, c10 = (pc >> 16) & 0xFF, c11 = (pc >> 24) & 0xFF;
+                    float a00, a01, a10, a11;
+                    if (i < m) {
+                        a00 = Xh[(size_t)c00 * A.m_pad + i]; a01 = Xh[(size_t)c01 * A.m_pad + i];
+                        a10 = Xh[(size_t)c10 * A.m_pad + i]; a11 = Xh[(size_t)c11 * A.m_pad + i];
+                    } else {
+                        a00 = xh_mean[c00]; a01 = xh_mean[c01]; a10 = xh_mean[c10]; a11 = xh_mean[c11];
+                    }
+                    const float sl = dir == 0 ? 0.5f * ((a01 + a11) - (a00 + a10))
+                                              : 0.5f * ((a10 + a11) - (a00 + a01));
+                    if (i < m) {
+                        val = sl * A.inv_sigma;
+                    } else {
+                        val = (A.y[dir * A.n_subv + A.tab.obs_sub[o0 + s]] - sl) * A.inv_sigma;
+                        dtv[k] = val;
+                    }
+                }
+                v[u] = val;
+            }
+            store8(opg_h, opg_l, i, kc * 8, KP, v, true);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, A.gram_terms, 0);
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
+        ph_mma ^= 1;
+        tc_fence_after();
+        // ---- 3a. read G and b; scale s = 1 + ||G||_F / c, an upper bound of cond((m-1)I + G)
+        auto read_gram = [&]() -> float {
+            float fro = 0.f;
+            for (int q = 0; q < half / 8; ++q) {
+                const int j0 = hh * half + q * 8;
+                float g[8];
+                tmem_ld8(tl + TM_G + j0, g);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = j0 + u;
+                    if (row < m && j < m) fro += g[u] * g[u];
+                    if (row < m && j == m) bvec[row] = g[u];
+                }
+            }
+            return block_sum(ctl, fro);
+        };
+        float fro = read_gram();
+        if (A.gram_terms < 3 && 1.f + sqrtf(fro) / c > A.s_split) {
+            // conditioning bound too large for single BF16 operands: add the high/low cross terms
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, 3, 0, 1);
+                mma_commit(&ctl->bar_mma);
+            }
+            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
+            ph_mma ^= 1;
+            tc_fence_after();
+            fro = read_gram();
+        }
+        const float s_scale = 1.f + sqrtf(fro) / c;
+        const float inv_cs = 1.f / (c * s_scale);
+        for (int q = 0; q < half / 8; ++q) {
+            const int j0 = hh * half + q * 8;
+            float g[8], yv[8], zv[8];
+            tmem_ld8(tl + TM_G + j0, g);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u;
+                const bool in = row < m && j < m;
+                const float id = (row == j) ? 1.f : 0.f;
+                yv[u] = in ? (id + g[u] / c) / s_scale : 0.f;
+                zv[u] = in ? id : 0.f;
+            }
+            store8(Yh, Yl, row, j0, NP, yv, true);
+            store8(Zh, Zl, row, j0, NP, zv, true);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // ---- 3b. coupled Newton-Schulz iteration
+        bool z_in_tmem = false;
+        float rn_prev = 3.0e38f;
+        int it = 0;
+        bool ok = true;
+        for (; it < A.max_it; ++it) {
+            if (tid == 0) {
+                tc_fence_after();
+                issue_product(tbase + TM_P, Zh, Zl, Yh, Yl, NP, NP, 3, 1);     // P = Z Y
+                mma_commit(&ctl->bar_mma);
+            }
+            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) { ok = false; break; }
+            ph_mma ^= 1;
+            tc_fence_after();
+            float r2 = 0.f;
+            for (int q = 0; q < half / 8; ++q) {
+                const int j0 = hh * half + q * 8;
+                float pv[8], tv[8];
+                tmem_ld8(tl + TM_P + j0, pv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = j0 + u;
+                    const bool in = row < m && j < m;
+                    const float id = (row == j) ? 1.f : 0.f;
+                    const float rr = id - pv[u];
+                    if (in) r2 += rr * rr;
+                    tv[u] = in ? 1.5f * id - 0.5f * pv[u] : 0.f;
+                }
+                store8(Th, Tl, row, j0, NP, tv, true);
+            }
+            r2 = block_sum(ctl, r2);
+            const float rn = sqrtf(r2);
+            const bool conv = rn < 2e-6f * (float)m || (rn < 2e-2f && rn > 0.6f * rn_prev);
+            rn_prev = rn;
+            if (conv) break;
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
+                issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
+                mma_commit(&ctl->bar_mma);   // one commit covers both products
+            }
+            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) { ok = false; break; }
+            ph_mma ^= 1;
+            tc_fence_after();
+            for (int q = 0; q < half / 8; ++q) {
+                const int j0 = hh * half + q * 8;
+                float yv[8], zv[8];
+                tmem_ld8(tl + TM_Y + j0, yv);
+                tmem_ld8(tl + TM_Z + j0, zv);
+                store8(Yh, Yl, row, j0, NP, yv, true);
+                store8(Zh, Zl, row, j0, NP, zv, true);
+            }
+            z_in_tmem = true;
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (!ok) break;
+        if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- 4. mean weights w_bar = Z (Z b) / (c s), one FP64-residual refinement
+        auto zrow = [&](int j0, float (&zv)[8]) {
+            if (z_in_tmem) {
+                tmem_ld8(tl + TM_Z + j0, zv);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) zv[u] = (row == j0 + u && row < m) ? 1.f : 0.f;
+            }
+        };
+        // y_out[row] = sum_j Z[row][j] x_in[j]  (all rows; rows >= m give 0)
+        auto zmatvec = [&](const float* x_in, float* y_out) {
+            float part = 0.f;
+            for (int q = 0; q < half / 8; ++q) {
+                const int j0 = hh * half + q * 8;
+                float zv[8];
+                zrow(j0, zv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (j0 + u < m) part += zv[u] * x_in[j0 + u];
+            }
+            vtmp[hh * 128 + row] = part;
+            __syncthreads();
+            if (hh == 0) y_out[row] = vtmp[row] + vtmp[128 + row];
+            __syncthreads();
+        };
+        zmatvec(bvec, vv);
+        zmatvec(vv, wbar);
+        if (hh == 0) wbar[row] = row < m ? wbar[row] * inv_cs : 0.f;
+        __syncthreads();
+        // Refinement against the exact operator: r = S^T (d/sigma - S w_bar) - (m-1) w_bar, with the
+        // FP32 slopes S recomputed from the halo rows (still in L2) and the member means, so
+        // the mean weights do not inherit the rounding of the tensor-core Gram.
+        auto slope_at = [&](int k, int i) -> float {
+            const int dir = k < n_obs ? 0 : 1;
+            const int sidx = k - dir * n_obs;
+            const int pc = A.tab.obs_corner[o0 + sidx];
+            const int c00 = pc & 0xFF, c01 = (pc >> 8) & 0xFF, c10 = (pc >> 16) & 0xFF, c11 = (pc >> 24) & 0xFF;
+            const float* Xg = A.X + (size_t)A.row_obs * A.m_pad + i;
+            const float a00 = Xg[(size_t)A.tab.halo[h0 + c00] * A.m_pad] - xh_mean[c00];
+            const float a01 = Xg[(size_t)A.tab.halo[h0 + c01] * A.m_pad] - xh_mean[c01];
+            const float a10 = Xg[(size_t)A.tab.halo[h0 + c10] * A.m_pad] - xh_mean[c10];
+            const float a11 = Xg[(size_t)A.tab.halo[h0 + c11] * A.m_pad] - xh_mean[c11];
+            const float sl = dir == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+            return sl * A.inv_sigma;
+        };
+        for (int ref = 0; ref < 2; ++ref) {
+            for (int k = warp; k < p_loc; k += FT / 32) {     // t = d/sigma - S w_bar, per slope
+                float part = 0.f;
+                for (int i = lane; i < m; i += 32) part += slope_at(k, i) * wbar[i];
+                part = warp_sum(part);
+                if (lane == 0) tvv[k] = dtv[k] - part;
+            }
+            __syncthreads();
+            {                                                   // r = S^T t - (m-1) w_bar, per member
+                const int i = tid & 127, kh = tid >> 7;
+                float part = 0.f;
+                if (i < m)
+                    for (int k = kh; k < p_loc; k += 2) part += slope_at(k, i) * tvv[k];
+                vtmp[kh * 128 + i] = part;
+                __syncthreads();
+                if (kh == 0) vv[i] = i < m ? vtmp[i] + vtmp[128 + i] - c * wbar[i] : 0.f;
+                __syncthreads();
+            }
+            zmatvec(vv, vr);             // Z r
+            zmatvec(vr, vv);             // Z (Z r)
+            if (hh == 0 && row < m) wbar[row] += vv[row] * inv_cs;
+            __syncthreads();
+        }
+        // ---- 5. transform: X_a[E] = x_bar 1^T + (X'_E w_bar) 1^T + centred(X'_E T).  In exact
+        //        arithmetic T 1 = 1 and X'_E 1 = 0, so X'_E T has zero member mean and this is
+        //        x_bar 1^T + X'_E (w_bar 1^T + T); centring the product keeps the analysis mean
+        //        exactly x_bar + X'_E w_bar whatever the rounding of T.
+        const float rs = rsqrtf(s_scale);
+        for (int q = 0; q < half / 8; ++q) {
+            const int j0 = hh * half + q * 8;
+            float zv[8], bv[8];
+            zrow(j0, zv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u;
+                bv[u] = (row < m && j < m) ? zv[u] * rs : 0.f;
+            }
+            store8(Bh, Bl, row, j0, NP, bv, A.tr_terms > 1);
+        }
+        for (int e = warp; e < n_e; e += FT / 32) {
+            float s = 0.f;
+            for (int i = lane; i < m; i += 32) s += XE[(size_t)e * A.m_pad + i];
+            s = warp_sum(s);
+            const float mu = s / (float)m;
+            double u = 0.0;    // mean update X'_E w_bar, summed in FP64
+            for (int i = lane; i < m; i += 32) u += (double)(XE[(size_t)e * A.m_pad + i] - mu) * (double)wbar[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+            if (lane == 0) {
+                xe_mean[e] = mu;
+                uvec[e] = (float)u;
+            }
+        }
+        __syncthreads();
+        for (int t = tid; t < MT * (NP >> 3); t += FT) {
+            const int e = t % MT, kc = t / MT;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = kc * 8 + u;
+                v[u] = (e < n_e && k < m) ? XE[(size_t)e * A.m_pad + k] - xe_mean[e] : 0.f;
+            }
+            store8(Ah, Al, e, kc * 8, NP, v, A.tr_terms > 1);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_P, Ah, Al, Bh, Bl, NP, NP, A.tr_terms, 1);   // X'_E W' 
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
+        ph_mma ^= 1;
+        tc_fence_after();
+        // ---- epilogue: analysis rows, forecast, prediction
+        float psum = 0.f;
+        const bool mine = row < n_e;
+        int grow = 0, jact = 0;
+        if (mine) {
+            jact = row < n_own ? A.tab.own[e0 + row] : A.tab.own[e0 + row - n_own];
+            grow = row < n_own ? jact : A.n_act + jact;
+        }
+        {   // member mean of this row of X'_E T (two column halves)
+            float part = 0.f;
+            for (int q = 0; q < half / 8; ++q) {
+                const int j0 = hh * half + q * 8;
+                float dv[8];
+                tmem_ld8(tl + TM_P + j0, dv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (j0 + u < m) part += dv[u];
+            }
+            vtmp[hh * 128 + row] = part;
+            __syncthreads();
+        }
+        const float shift = mine ? xe_mean[row] + uvec[row] - (vtmp[row] + vtmp[128 + row]) / (float)m : 0.f;
+        __syncthreads();
+        for (int q = 0; q < half / 8; ++q) {
+            const int j0 = hh * half + q * 8;
+            float dv[8];
+            tmem_ld8(tl + TM_P + j0, dv);
+            if (!mine) continue;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u;
+                if (j >= m) continue;
+                const float xa = shift + dv[u];
+                if (A.with_forecast) {
+                    float v = 0.f;
+                    if (A.vmode == 0) {
+                        v = A.V[(size_t)jact * A.m_pad + j];
+                    } else if (A.vmode == 1) {
+                        float zz[4];
+                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
+                        v = A.q_white * zz[jact & 3];
+                    }
+                    const float n1 = A.a * xa + v;
+                    A.Xo[(size_t)jact * A.m_pad + j] = n1;
+                    A.Xo[(size_t)(A.n_act + jact) * A.m_pad + j] = xa;
+                    psum += n1;
+                } else {
+                    A.Xo[(size_t)grow * A.m_pad + j] = xa;
+                }
+            }
+        }
+        if (A.with_forecast) {
+            vtmp[hh * 128 + row] = psum;
+            __syncthreads();
+            if (hh == 0 && mine && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tbase, TM_COLS);
+}
+
+// Self-test of the tensor-core product: D (128 x N) = A (128 x K) * B (N x K)^T, operands
+// split into BF16 high/low parts (terms = 1: high only; 3: three products).
+__global__ void __launch_bounds__(FT, 1) umma_selftest_kernel(const float* __restrict__ Ag, const float* __restrict__ Bg,
+                                                              float* __restrict__ Dg, int N, int K, int terms,
+                                                              int b_mn, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Ctrl* ctl = reinterpret_cast<Ctrl*>(smem);
+    const int szA = MT * K * 2, szB = N * K * 2;
+    unsigned char* a_h = smem + 1024;
+    unsigned char* a_l = a_h + szA;
+    unsigned char* b_h = a_l + szA;
+    unsigned char* b_l = b_h + szB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&ctl->bar_mma, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&ctl->tmem_base, 256);
+        tmem_relinquish();
+    }
+    for (int t = tid; t < MT * (K >> 3); t += FT) {
+        const int r = t / (K >> 3), kc = t % (K >> 3);
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = Ag[(size_t)r * K + kc * 8 + u];
+        store8(a_h, a_l, r, kc * 8, K, v, true);
+    }
+    if (b_mn) {   // B given as K rows x N columns
+        for (int t = tid; t < K * (N >> 3); t += FT) {
+            const int r = t / (N >> 3), nc = t % (N >> 3);
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = Bg[(size_t)r * N + nc * 8 + u];
+            store8(b_h, b_l, r, nc * 8, N, v, true);
+        }
+    } else {      // B given as N rows x K columns
+        for (int t = tid; t < N * (K >> 3); t += FT) {
+            const int r = t / (K >> 3), kc = t % (K >> 3);
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = Bg[(size_t)r * K + kc * 8 + u];
+            store8(b_h, b_l, r, kc * 8, K, v, true);
+        }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ctl->tmem_base;
+    if (tid == 0) {
+        issue_product(tbase, a_h, a_l, b_h, b_l, K, N, terms, b_mn);
+        mma_commit(&ctl->bar_mma);
+    }
+    if (wait_all(ctl, &ctl->bar_mma, 0, status)) {
+        tc_fence_after();
+        const int row = 32 * (warp & 3) + lane;
+        const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+        // warps 0-3 and 4-7 split the columns
+        const int hh = warp >> 2, hn = N / 2;
+        for (int q = 0; q < hn / 8; ++q) {
+            float v[8];
+            const int j0 = hh * hn + q * 8;
+            tmem_ld8(tl + j0, v);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) Dg[(size_t)row * N + j0 + u] = v[u];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tbase, 256);
+}
+
+int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+int fused_prepare(letkf_ctx* c) {
+    const HostModel& h = c->host;
+    const int m = c->m;
+    const int NP = round_up(m + 1, 16);
+    const int KP = std::max(16, round_up(h.p_loc_max, 16));
+    if (NP > MT || KP > MT) return LETKF_EINVAL;   // m <= 127, at most 128 slopes per domain
+    const int sz_op = MT * NP * 2;
+    const int sz_opg = MT * KP * 2;
+    const int xh_bytes = round_up(std::max(h.n_h_max, 1) * c->m_pad * 4, 1024);
+    const int big = std::max(xh_bytes + 2 * sz_opg, 6 * sz_op);
+    const int off_vec = 1024;
+    const int off_xe = off_vec + 8192;
+    const int xe_bytes = round_up(std::max(h.n_loc_max, 1) * c->m_pad * 4, 1024);
+    const int off_big = round_up(off_xe + xe_bytes, 1024);
+    const int total = off_big + big;
+    if (total > 227 * 1024) return LETKF_EINVAL;
+    if (h.n_h_max > 255 || h.n_loc_max > MT) return LETKF_EINVAL;
+    c->fused_smem = total;
+    if (cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, total) != cudaSuccess)
+        return LETKF_ECUDA;
+    c->fused_grid = std::min(c->sms, c->n_dom);
+    return LETKF_OK;
+}
+
+int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast) {
+    if (sigma > 0) c->sigma = sigma;
+    int rc = launch_precheck(c, y);    // also resets the work queue
+    if (rc) return rc;
+    FusedArgs A;
+    A.X = static_cast<const float*>(c->X[c->cur]);
+    A.Xo = static_cast<float*>(c->X[c->cur ^ 1]);
+    A.y = static_cast<const float*>(y);
+    A.V = nullptr;
+    A.vmode = 2;
+    if (with_forecast) {
+        if (c->Lq) {
+            if ((rc = draw_perturbations(c, c->frame))) return rc;
+            A.V = static_cast<const float*>(c->V);
+            A.vmode = 0;
+        } else if (c->q_white > 0) {
+            A.vmode = 1;
+        }
+    }
+    A.xpred = static_cast<float*>(xpred);
+    A.tab = c->tab;
+    A.status = c->d_status;
+    A.frame_bad = c->d_frame_bad;
+    A.queue = c->d_queue;
+    A.m = c->m;
+    A.m_pad = c->m_pad;
+    A.n_act = c->n_act;
+    A.n_subv = c->n_subv;
+    A.n_dom = c->n_dom;
+    A.row_obs = c->obs_block == 1 ? c->n_act : 0;
+    A.NP = round_up(c->m + 1, 16);
+    A.KP = std::max(16, round_up(c->host.p_loc_max, 16));
+    A.inv_sigma = (float)(1.0 / c->sigma);
+    A.a = (float)c->a;
+    A.q_white = (float)c->q_white;
+    A.with_forecast = with_forecast;
+    A.gram_terms = c->precision == LETKF_PREC_MIXED ? 1 : 3;
+    A.tr_terms = c->precision == LETKF_PREC_MIXED ? 1 : 3;
+    A.max_it = 40;
+    A.s_split = 8.0f;
+    A.seed = c->seed;
+    A.frame = (uint32_t)c->frame;
+    const int sz_op = MT * A.NP * 2;
+    const int sz_opg = MT * A.KP * 2;
+    A.off_vec = 1024;
+    A.off_xe = A.off_vec + 8192;
+    const int xe_bytes = round_up(std::max(c->host.n_loc_max, 1) * c->m_pad * 4, 1024);
+    A.off_big = round_up(A.off_xe + xe_bytes, 1024);
+    A.off_opg = round_up(std::max(c->host.n_h_max, 1) * c->m_pad * 4, 1024);
+    A.sz_op = sz_op;
+    A.sz_opg = sz_opg;
+    prof_begin(c, STAGE_FUSED);
+    fused_kernel<<<c->fused_grid, FT, c->fused_smem, c->stream>>>(A);
+    prof_end(c);
+    return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
+}
+
+}  // namespace letkf
+
+extern "C" int letkf_umma_selftest(const float* A, const float* B, float* D, int n, int k, int terms, int b_layout,
+                                   void* stream) {
+    using namespace letkf;
+    if (!A || !B || !D || n < 16 || n > 256 || (n % 16) || k < 16 || k > 128 || (k % 16) ||
+        (terms != 1 && terms != 3) || (b_layout != 0 && b_layout != 1))
+        return LETKF_EINVAL;
+    const int smem = 1024 + 2 * (MT * k * 2) + 2 * (n * k * 2);
+    if (cudaFuncSetAttribute(umma_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return LETKF_ECUDA;
+    int* st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) return LETKF_ENOMEM;
+    cudaMemsetAsync(st, 0, sizeof(int), (cudaStream_t)stream);
+    umma_selftest_kernel<<<1, FT, smem, (cudaStream_t)stream>>>(A, B, D, n, k, terms, b_layout, st);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    cudaError_t e2 = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(st);
+    if (e != cudaSuccess || e2 != cudaSuccess) return LETKF_ECUDA;
+    return h ? LETKF_ETIMEOUT : LETKF_OK;
+}

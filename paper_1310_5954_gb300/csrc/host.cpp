@@ -1,0 +1,581 @@
+// Host side of libletkf: geometry, domain decomposition, context life cycle and the C ABI.
+//
+// Geometry (Sect. 3): circular (optionally annular) pupil, a subaperture is
+// valid when at least half of its area is illuminated (20 x 20 midpoint
+// sampling, outer edge compared in exact integers); Fried actuators are the
+// corners of valid subapertures.  Domains (Sect. 2.3): dom_sub x dom_sub blocks
+// of subapertures own their actuators (the last actuator row and column fold
+// into the last block); a domain observes the valid subapertures of its block
+// grown by `halo` subapertures, both slope directions.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.hpp"
+
+using letkf::HostModel;
+
+namespace {
+
+#define CU(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return LETKF_ECUDA;                   \
+    } while (0)
+
+std::vector<uint8_t> pupil_mask(int n, double obstruction) {
+    const int q = 20;
+    std::vector<uint8_t> mask((size_t)n * n, 0);
+    const long long R2 = (long long)(q * n) * (q * n);
+    const double rin = obstruction * q * n;
+    const double rin2 = rin * rin;
+    for (int r = 0; r < n; ++r) {
+        for (int c = 0; c < n; ++c) {
+            int inside = 0;
+            for (int t = 0; t < q; ++t) {
+                const long long b = 2LL * q * r + 2 * t + 1 - (long long)q * n;
+                for (int s = 0; s < q; ++s) {
+                    const long long a = 2LL * q * c + 2 * s + 1 - (long long)q * n;
+                    const long long d2 = a * a + b * b;
+                    if (d2 <= R2 && (double)d2 >= rin2) ++inside;
+                }
+            }
+            mask[(size_t)r * n + c] = (2 * inside >= q * q) ? 1 : 0;
+        }
+    }
+    return mask;
+}
+
+// Orthonormal basis Q (p x r, column-major) of the column space of A (p x n,
+// column-major) by Householder QR with column pivoting, rank by a relative
+// pivot threshold.  Returns r.
+int range_basis(const std::vector<double>& A_in, int p, int n, std::vector<double>& Q) {
+    std::vector<double> A = A_in;
+    std::vector<int> perm(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::vector<double> norms(n);
+    double max0 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s = 0;
+        for (int i = 0; i < p; ++i) s += A[(size_t)j * p + i] * A[(size_t)j * p + i];
+        norms[j] = s;
+        max0 = std::max(max0, s);
+    }
+    const int kmax = std::min(p, n);
+    std::vector<std::vector<double>> hv;  // Householder vectors (length p, zeros above k)
+    std::vector<double> beta;
+    int r = 0;
+    for (int k = 0; k < kmax; ++k) {
+        // recompute remaining norms on rows k..p-1 (robust, sizes are small)
+        int piv = -1;
+        double best = -1.0;
+        for (int j = k; j < n; ++j) {
+            double s = 0;
+            for (int i = k; i < p; ++i) s += A[(size_t)j * p + i] * A[(size_t)j * p + i];
+            if (s > best) { best = s; piv = j; }
+        }
+        if (best <= 1e-20 * std::max(max0, 1e-300)) break;
+        if (piv != k) {
+            for (int i = 0; i < p; ++i) std::swap(A[(size_t)k * p + i], A[(size_t)piv * p + i]);
+            std::swap(perm[k], perm[piv]);
+        }
+        std::vector<double> v(p, 0.0);
+        double alpha = 0;
+        for (int i = k; i < p; ++i) alpha += A[(size_t)k * p + i] * A[(size_t)k * p + i];
+        alpha = std::sqrt(alpha);
+        const double x0 = A[(size_t)k * p + k];
+        if (x0 > 0) alpha = -alpha;
+        for (int i = k; i < p; ++i) v[i] = A[(size_t)k * p + i];
+        v[k] -= alpha;
+        double vv = 0;
+        for (int i = k; i < p; ++i) vv += v[i] * v[i];
+        const double bt = vv > 0 ? 2.0 / vv : 0.0;
+        for (int j = k; j < n; ++j) {
+            double s = 0;
+            for (int i = k; i < p; ++i) s += v[i] * A[(size_t)j * p + i];
+            s *= bt;
+            for (int i = k; i < p; ++i) A[(size_t)j * p + i] -= s * v[i];
+        }
+        hv.push_back(v);
+        beta.push_back(bt);
+        r = k + 1;
+    }
+    // Q = H_0 H_1 ... H_{r-1} [I_r; 0]
+    Q.assign((size_t)p * r, 0.0);
+    for (int j = 0; j < r; ++j) Q[(size_t)j * p + j] = 1.0;
+    for (int k = r - 1; k >= 0; --k) {
+        const std::vector<double>& v = hv[k];
+        for (int j = 0; j < r; ++j) {
+            double s = 0;
+            for (int i = k; i < p; ++i) s += v[i] * Q[(size_t)j * p + i];
+            s *= beta[k];
+            for (int i = k; i < p; ++i) Q[(size_t)j * p + i] -= s * v[i];
+        }
+    }
+    return r;
+}
+
+void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obstruction, int b, int halo,
+                 bool factors) {
+    h.n_sub = n;
+    if (sub_valid) {
+        h.sub_valid.assign(sub_valid, sub_valid + (size_t)n * n);
+        for (auto& v : h.sub_valid) v = v ? 1 : 0;
+    } else {
+        h.sub_valid = pupil_mask(n, obstruction);
+    }
+    const int na = n + 1;
+    h.act_valid.assign((size_t)na * na, 0);
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c)
+            if (h.sub_valid[(size_t)r * n + c]) {
+                h.act_valid[(size_t)r * na + c] = 1;
+                h.act_valid[(size_t)r * na + c + 1] = 1;
+                h.act_valid[(size_t)(r + 1) * na + c] = 1;
+                h.act_valid[(size_t)(r + 1) * na + c + 1] = 1;
+            }
+    h.sub_index.assign((size_t)n * n, -1);
+    h.act_index.assign((size_t)na * na, -1);
+    h.sub_rc.clear();
+    h.act_rc.clear();
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c)
+            if (h.sub_valid[(size_t)r * n + c]) {
+                h.sub_index[(size_t)r * n + c] = (int)(h.sub_rc.size() / 2);
+                h.sub_rc.push_back(r);
+                h.sub_rc.push_back(c);
+            }
+    for (int r = 0; r < na; ++r)
+        for (int c = 0; c < na; ++c)
+            if (h.act_valid[(size_t)r * na + c]) {
+                h.act_index[(size_t)r * na + c] = (int)(h.act_rc.size() / 2);
+                h.act_rc.push_back(r);
+                h.act_rc.push_back(c);
+            }
+    h.n_subv = (int)(h.sub_rc.size() / 2);
+    h.n_act = (int)(h.act_rc.size() / 2);
+
+    const int nb = (n + b - 1) / b;
+    h.own_off = {0};
+    h.obs_off = {0};
+    h.halo_off = {0};
+    h.own.clear(); h.obs_sub.clear(); h.obs_corner.clear(); h.halo.clear();
+    h.rank.clear(); h.fac_off.clear(); h.fac.clear();
+    h.n_loc_max = h.p_loc_max = h.n_h_max = h.rank_max = 0;
+    std::map<std::vector<int>, std::pair<int, int>> cache;  // local pattern -> (rank, fac_off)
+    std::vector<double> cost;
+    for (int I = 0; I < nb; ++I) {
+        for (int J = 0; J < nb; ++J) {
+            std::vector<int> owned;
+            for (int r = 0; r <= n; ++r) {
+                if (std::min(r / b, nb - 1) != I) continue;
+                for (int c = 0; c <= n; ++c) {
+                    if (std::min(c / b, nb - 1) != J) continue;
+                    const int k = h.act_index[(size_t)r * na + c];
+                    if (k >= 0) owned.push_back(k);
+                }
+            }
+            if (owned.empty()) continue;
+            std::sort(owned.begin(), owned.end());
+            std::vector<int> subs;
+            for (int r = std::max(0, b * I - halo); r < std::min(n, b * (I + 1) + halo); ++r)
+                for (int c = std::max(0, b * J - halo); c < std::min(n, b * (J + 1) + halo); ++c) {
+                    const int k = h.sub_index[(size_t)r * n + c];
+                    if (k >= 0) subs.push_back(k);
+                }
+            std::sort(subs.begin(), subs.end());
+            std::vector<int> hal;
+            for (int s : subs) {
+                const int r = h.sub_rc[2 * s], c = h.sub_rc[2 * s + 1];
+                hal.push_back(h.act_index[(size_t)r * na + c]);
+                hal.push_back(h.act_index[(size_t)r * na + c + 1]);
+                hal.push_back(h.act_index[(size_t)(r + 1) * na + c]);
+                hal.push_back(h.act_index[(size_t)(r + 1) * na + c + 1]);
+            }
+            std::sort(hal.begin(), hal.end());
+            hal.erase(std::unique(hal.begin(), hal.end()), hal.end());
+            std::vector<int> corners;
+            for (int s : subs) {
+                const int r = h.sub_rc[2 * s], c = h.sub_rc[2 * s + 1];
+                const int ids[4] = {h.act_index[(size_t)r * na + c], h.act_index[(size_t)r * na + c + 1],
+                                    h.act_index[(size_t)(r + 1) * na + c], h.act_index[(size_t)(r + 1) * na + c + 1]};
+                int packed = 0;
+                for (int t = 0; t < 4; ++t) {
+                    const int loc = (int)(std::lower_bound(hal.begin(), hal.end(), ids[t]) - hal.begin());
+                    packed |= (loc & 0xFF) << (8 * t);
+                }
+                corners.push_back(packed);
+            }
+            for (int k : owned) h.own.push_back(k);
+            for (size_t t = 0; t < subs.size(); ++t) {
+                h.obs_sub.push_back(subs[t]);
+                h.obs_corner.push_back(corners[t]);
+            }
+            for (int k : hal) h.halo.push_back(k);
+            h.own_off.push_back((int)h.own.size());
+            h.obs_off.push_back((int)h.obs_sub.size());
+            h.halo_off.push_back((int)h.halo.size());
+            const int n_loc = 2 * (int)owned.size(), p_loc = 2 * (int)subs.size(), n_h = (int)hal.size();
+            h.n_loc_max = std::max(h.n_loc_max, n_loc);
+            h.p_loc_max = std::max(h.p_loc_max, p_loc);
+            h.n_h_max = std::max(h.n_h_max, n_h);
+            int rk = 0, off = 0;
+            if (factors && p_loc > 0) {
+                // pattern key: sizes plus the packed corner list (local structure of D_loc)
+                std::vector<int> key = {n_h, p_loc};
+                key.insert(key.end(), corners.begin(), corners.end());
+                auto it = cache.find(key);
+                if (it != cache.end()) {
+                    rk = it->second.first;
+                    off = it->second.second;
+                } else {
+                    // D_loc (p_loc x n_h) column-major: x-slopes then y-slopes (Fried, Sect. 3)
+                    const int ns = (int)subs.size();
+                    std::vector<double> D((size_t)p_loc * n_h, 0.0);
+                    for (int s = 0; s < ns; ++s) {
+                        const int c00 = corners[s] & 0xFF, c01 = (corners[s] >> 8) & 0xFF;
+                        const int c10 = (corners[s] >> 16) & 0xFF, c11 = (corners[s] >> 24) & 0xFF;
+                        D[(size_t)c01 * p_loc + s] += 0.5; D[(size_t)c11 * p_loc + s] += 0.5;
+                        D[(size_t)c00 * p_loc + s] -= 0.5; D[(size_t)c10 * p_loc + s] -= 0.5;
+                        D[(size_t)c10 * p_loc + ns + s] += 0.5; D[(size_t)c11 * p_loc + ns + s] += 0.5;
+                        D[(size_t)c00 * p_loc + ns + s] -= 0.5; D[(size_t)c01 * p_loc + ns + s] -= 0.5;
+                    }
+                    std::vector<double> Q;
+                    rk = range_basis(D, p_loc, n_h, Q);
+                    off = (int)h.fac.size();
+                    // F^T = Q^T D (r x n_h) row-major, then Q^T (r x p_loc) row-major
+                    for (int i = 0; i < rk; ++i)
+                        for (int j = 0; j < n_h; ++j) {
+                            double s = 0;
+                            for (int t = 0; t < p_loc; ++t) s += Q[(size_t)i * p_loc + t] * D[(size_t)j * p_loc + t];
+                            h.fac.push_back((float)s);
+                        }
+                    for (int i = 0; i < rk; ++i)
+                        for (int t = 0; t < p_loc; ++t) h.fac.push_back((float)Q[(size_t)i * p_loc + t]);
+                    cache[key] = {rk, off};
+                }
+            }
+            h.rank.push_back(rk);
+            h.fac_off.push_back(off);
+            h.rank_max = std::max(h.rank_max, rk);
+            cost.push_back((double)p_loc * 1e6 + (double)n_loc);
+        }
+    }
+    const int nd = (int)h.own_off.size() - 1;
+    h.order.resize(nd);
+    std::iota(h.order.begin(), h.order.end(), 0);
+    std::stable_sort(h.order.begin(), h.order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+}
+
+template <typename V>
+int upload(letkf_ctx* c, const std::vector<V>& h, V** d) {
+    *d = nullptr;
+    if (h.empty()) return LETKF_OK;
+    CU(cudaMalloc((void**)d, h.size() * sizeof(V)));
+    c->device_bytes += h.size() * sizeof(V);
+    CU(cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return LETKF_OK;
+}
+
+int alloc(letkf_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return LETKF_OK;
+    if (cudaMalloc(p, bytes) != cudaSuccess) return LETKF_ENOMEM;
+    c->device_bytes += bytes;
+    CU(cudaMemset(*p, 0, bytes));
+    return LETKF_OK;
+}
+
+void free_all(letkf_ctx* c) {
+    void* ptrs[] = {c->X[0], c->X[1], c->Lq, c->Xi, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
+                    c->d_status, c->d_frame_bad, c->d_queue, c->tab.own_off, c->tab.own, c->tab.obs_off,
+                    c->tab.obs_sub, c->tab.obs_corner, c->tab.halo_off, c->tab.halo, c->tab.order,
+                    c->tab.rank, c->tab.fac_off, c->tab.fac};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->cublas) cublasDestroy(c->cublas);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+}
+
+int create_impl(const letkf_params* p, letkf_ctx* c) {
+    if (p->n_sub < 1 || p->n_sub > 1024 || p->m < 2 || p->m > 256 || p->dom_sub < 1 || p->halo < 0 ||
+        !(p->sigma > 0) || !(std::fabs(p->ar1_a) < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
+        p->precision < 0 || p->precision > 2 || p->path < 0 || p->path > 1 || p->q_white < 0 ||
+        !(p->obstruction >= 0 && p->obstruction < 1))
+        return LETKF_EINVAL;
+    if (p->precision == LETKF_PREC_FP64 && p->path != LETKF_PATH_PLAIN) return LETKF_EINVAL;
+    if (p->precision == LETKF_PREC_MIXED && p->path != LETKF_PATH_FUSED) return LETKF_EINVAL;
+    if (p->path == LETKF_PATH_PLAIN && !letkf::plain_limits_ok(p->precision, p->m)) return LETKF_EINVAL;
+    if (p->dom_sub + 2 * p->halo > 14) return LETKF_EINVAL;  // halo tile must fit the byte-packed corners
+    c->n_sub = p->n_sub; c->m = p->m; c->dom_sub = p->dom_sub; c->halo = p->halo;
+    c->precision = p->precision; c->path = p->path; c->obs_block = p->obs_block; c->device = p->device;
+    c->a = p->ar1_a; c->sigma = p->sigma; c->q_white = p->q_white; c->seed = p->seed;
+    c->stream = (cudaStream_t)p->stream;
+    const int eb = c->precision == LETKF_PREC_FP64 ? 8 : 4;
+    c->m_pad = (eb == 8) ? ((c->m + 1) / 2) * 2 : ((c->m + 3) / 4) * 4;
+    c->mb_pad = ((c->m + 7) / 8) * 8;
+    CU(cudaSetDevice(c->device));
+    CU(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    build_model(c->host, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo, c->path == LETKF_PATH_FUSED);
+    HostModel& h = c->host;
+    c->n_act = h.n_act; c->n_subv = h.n_subv; c->n = 2 * h.n_act; c->p = 2 * h.n_subv;
+    c->n_dom = (int)h.own_off.size() - 1;
+    if (c->n_act == 0 || c->n_dom == 0) return LETKF_EINVAL;
+    int rc;
+    c->tab.n_dom = c->n_dom;
+    if ((rc = upload(c, h.own_off, &c->tab.own_off))) return rc;
+    if ((rc = upload(c, h.own, &c->tab.own))) return rc;
+    if ((rc = upload(c, h.obs_off, &c->tab.obs_off))) return rc;
+    if ((rc = upload(c, h.obs_sub, &c->tab.obs_sub))) return rc;
+    if ((rc = upload(c, h.obs_corner, &c->tab.obs_corner))) return rc;
+    if ((rc = upload(c, h.halo_off, &c->tab.halo_off))) return rc;
+    if ((rc = upload(c, h.halo, &c->tab.halo))) return rc;
+    if ((rc = upload(c, h.order, &c->tab.order))) return rc;
+    if (c->path == LETKF_PATH_FUSED) {
+        if ((rc = upload(c, h.rank, &c->tab.rank))) return rc;
+        if ((rc = upload(c, h.fac_off, &c->tab.fac_off))) return rc;
+        if ((rc = upload(c, h.fac, &c->tab.fac))) return rc;
+    }
+    const size_t row = (size_t)c->m_pad * eb;
+    if ((rc = alloc(c, &c->X[0], (size_t)c->n * row))) return rc;
+    if ((rc = alloc(c, &c->X[1], (size_t)c->n * row))) return rc;
+    if ((rc = alloc(c, &c->V, (size_t)c->n_act * row))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_frame_bad, sizeof(int)))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_queue, 2 * sizeof(int)))) return rc;
+    if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
+    if (cublasSetStream(c->cublas, c->stream) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
+    if (c->path == LETKF_PATH_PLAIN) {
+        std::vector<int> so(c->n_dom);
+        int acc = 0;
+        for (int d = 0; d < c->n_dom; ++d) {
+            so[d] = acc;
+            acc += 2 * (h.obs_off[d + 1] - h.obs_off[d]);
+        }
+        c->total_slopes = acc;
+        if ((rc = upload(c, so, &c->so_off))) return rc;
+        if ((rc = alloc(c, &c->S, (size_t)std::max(acc, 1) * row))) return rc;
+        if ((rc = alloc(c, &c->dt, (size_t)std::max(acc, 1) * eb))) return rc;
+        if ((rc = alloc(c, &c->G, (size_t)c->n_dom * c->m * row))) return rc;
+        if ((rc = alloc(c, &c->b, (size_t)c->n_dom * row))) return rc;
+        if ((rc = alloc(c, &c->W, (size_t)c->n_dom * c->m * row))) return rc;
+    } else {
+        if ((rc = letkf::fused_prepare(c))) return rc;
+    }
+    if ((rc = letkf::init_ensemble(c, p->q_sqrt, p->p0_sqrt))) return rc;
+    CU(cudaStreamSynchronize(c->stream));
+    c->cur = 0;
+    c->phase = 0;
+    c->frame = 0;
+    return LETKF_OK;
+}
+
+}  // namespace
+
+namespace letkf {
+int state_bytes(const letkf_ctx* c) { return c->precision == LETKF_PREC_FP64 ? 8 : 4; }
+
+void prof_begin(letkf_ctx* c, int stage) {
+    if (!c->prof_on) return;
+    if (c->prof_used + 2 > c->prof_ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            c->prof_ev.push_back(e);
+        }
+    }
+    c->prof_stage.push_back(stage);
+    cudaEventRecord(c->prof_ev[c->prof_used], c->stream);
+    c->prof_used += 2;
+}
+
+void prof_end(letkf_ctx* c) {
+    if (!c->prof_on || c->prof_used < 2) return;
+    cudaEventRecord(c->prof_ev[c->prof_used - 1], c->stream);
+}
+}  // namespace letkf
+
+extern "C" {
+
+int letkf_create(const letkf_params* params, letkf_ctx** out) {
+    if (!out) return LETKF_EINVAL;
+    *out = nullptr;
+    if (!params) return LETKF_EINVAL;
+    letkf_ctx* c = new (std::nothrow) letkf_ctx();
+    if (!c) return LETKF_ENOMEM;
+    int rc = create_impl(params, c);
+    if (rc != LETKF_OK) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return LETKF_OK;
+}
+
+int letkf_destroy(letkf_ctx* c) {
+    if (!c) return LETKF_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return LETKF_OK;
+}
+
+int letkf_get_info(const letkf_ctx* c, letkf_info* o) {
+    if (!c || !o) return LETKF_EINVAL;
+    o->n_sub = c->n_sub; o->n_act = c->n_act; o->n_subv = c->n_subv; o->n = c->n; o->p = c->p; o->m = c->m;
+    o->n_domains = c->n_dom; o->n_loc_max = c->host.n_loc_max; o->p_loc_max = c->host.p_loc_max;
+    o->rank_max = c->host.rank_max; o->state_bytes = letkf::state_bytes(c);
+    o->precision = c->precision; o->path = c->path; o->frame = c->frame; o->device_bytes = c->device_bytes;
+    return LETKF_OK;
+}
+
+int letkf_get_geometry(const letkf_ctx* c, unsigned char* sub_valid, unsigned char* act_valid) {
+    if (!c) return LETKF_EINVAL;
+    if (sub_valid) std::memcpy(sub_valid, c->host.sub_valid.data(), c->host.sub_valid.size());
+    if (act_valid) std::memcpy(act_valid, c->host.act_valid.data(), c->host.act_valid.size());
+    return LETKF_OK;
+}
+
+int letkf_analyze(letkf_ctx* c, const void* y, double sigma) {
+    if (!c || !y) return LETKF_EINVAL;
+    if (c->phase != 0) return LETKF_ESTATE;
+    CU(cudaSetDevice(c->device));
+    int rc;
+    if (c->path == LETKF_PATH_PLAIN) {
+        rc = letkf::plain_analyze(c, y, sigma);
+    } else {
+        rc = letkf::fused_step(c, y, sigma, nullptr, 0);
+    }
+    if (rc) return rc;
+    c->cur ^= 1;
+    c->phase = 1;
+    return LETKF_OK;
+}
+
+int letkf_forecast(letkf_ctx* c, const void* v) {
+    if (!c) return LETKF_EINVAL;
+    CU(cudaSetDevice(c->device));
+    int rc = letkf::launch_forecast(c, v, nullptr, c->phase);
+    if (rc) return rc;
+    c->phase = 0;
+    c->frame += 1;
+    return LETKF_OK;
+}
+
+int letkf_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
+    if (!c || !y) return LETKF_EINVAL;
+    if (c->phase != 0) return LETKF_ESTATE;
+    CU(cudaSetDevice(c->device));
+    int rc;
+    if (c->path == LETKF_PATH_PLAIN) {
+        if ((rc = letkf::plain_analyze(c, y, sigma))) return rc;
+        c->cur ^= 1;
+        if ((rc = letkf::launch_forecast(c, nullptr, xpred, 1))) return rc;
+    } else {
+        if ((rc = letkf::fused_step(c, y, sigma, xpred, 1))) return rc;
+        c->cur ^= 1;
+    }
+    c->phase = 0;
+    c->frame += 1;
+    return LETKF_OK;
+}
+
+int letkf_get_state(letkf_ctx* c, void* x, unsigned long long* frame) {
+    if (!c) return LETKF_EINVAL;
+    CU(cudaSetDevice(c->device));
+    if (x) {
+        const size_t eb = letkf::state_bytes(c);
+        CU(cudaMemcpy2DAsync(x, c->m * eb, c->X[c->cur], c->m_pad * eb, c->m * eb, c->n,
+                             cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (frame) *frame = c->frame;
+    return LETKF_OK;
+}
+
+int letkf_set_state(letkf_ctx* c, const void* x, unsigned long long frame) {
+    if (!c || !x) return LETKF_EINVAL;
+    CU(cudaSetDevice(c->device));
+    const size_t eb = letkf::state_bytes(c);
+    CU(cudaMemcpy2DAsync(c->X[c->cur], c->m_pad * eb, x, c->m * eb, c->m * eb, c->n,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    c->frame = frame;
+    c->phase = 0;
+    return LETKF_OK;
+}
+
+int letkf_sync(letkf_ctx* c) {
+    if (!c) return LETKF_EINVAL;
+    CU(cudaSetDevice(c->device));
+    CU(cudaStreamSynchronize(c->stream));
+    int st = 0;
+    CU(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) CU(cudaMemset(c->d_status, 0, sizeof(int)));
+    if (st & letkf::ST_TIMEOUT) return LETKF_ETIMEOUT;
+    if (st & letkf::ST_NONFINITE) return LETKF_ENONFINITE;
+    if (st & letkf::ST_NOCONV) return LETKF_ENOCONV;
+    return LETKF_OK;
+}
+
+int letkf_profile(letkf_ctx* c, int enable, letkf_stage_times* out) {
+    if (!c) return LETKF_EINVAL;
+    CU(cudaSetDevice(c->device));
+    if (enable) {
+        c->prof_stage.clear();
+        c->prof_used = 0;
+        c->prof_on = 1;
+        return LETKF_OK;
+    }
+    c->prof_on = 0;
+    CU(cudaStreamSynchronize(c->stream));
+    if (out) {
+        for (int i = 0; i < LETKF_N_STAGES; ++i) {
+            out->ms[i] = 0.0;
+            out->launches[i] = 0;
+        }
+        for (size_t r = 0; r < c->prof_stage.size(); ++r) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, c->prof_ev[2 * r], c->prof_ev[2 * r + 1]));
+            const int st = c->prof_stage[r];
+            if (st >= 0 && st < LETKF_N_STAGES) {
+                out->ms[st] += ms;
+                out->launches[st] += 1;
+            }
+        }
+    }
+    c->prof_stage.clear();
+    c->prof_used = 0;
+    return LETKF_OK;
+}
+
+const char* letkf_stage_name(int s) {
+    static const char* names[LETKF_N_STAGES] = {"slope_check", "noise_draw", "observed_anomalies", "gram",
+                                               "eigensolve_weights", "transform", "forecast",
+                                               "fused_analysis_forecast"};
+    return (s >= 0 && s < LETKF_N_STAGES) ? names[s] : "unknown";
+}
+
+const char* letkf_status_string(int s) {
+    switch (s) {
+        case LETKF_OK: return "ok";
+        case LETKF_EINVAL: return "invalid argument or unsupported configuration";
+        case LETKF_ENOMEM: return "out of memory";
+        case LETKF_ECUDA: return "CUDA or cuBLAS call failed";
+        case LETKF_ETIMEOUT: return "a bounded device-side wait gave up";
+        case LETKF_ENONFINITE: return "non-finite slopes: frame rejected, state unchanged";
+        case LETKF_ESTATE: return "call out of order";
+        case LETKF_ENOCONV: return "an eigensolve reached its sweep limit";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal definitions shared by the host code and the kernel files of libletkf.
+#pragma once
+
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/letkf.h"
+
+namespace letkf {
+
+// Bits of the device status word (latched until letkf_sync reads them).
+enum : int {
+    ST_NONFINITE = 1,   // a frame's slopes held a NaN or Inf; the frame was rejected
+    ST_NOCONV = 2,      // an eigensolve hit its sweep limit
+    ST_TIMEOUT = 4,     // a bounded wait on an mbarrier gave up
+};
+
+// Device-side domain tables, flattened over domains.  All indices are int32.
+struct DomainTables {
+    int n_dom = 0;
+    int* own_off = nullptr;     // [n_dom+1] into own
+    int* own = nullptr;         // owned valid-actuator indices
+    int* obs_off = nullptr;     // [n_dom+1] into obs_sub / obs_corner (observed subapertures)
+    int* obs_sub = nullptr;     // valid-subaperture index of each observed subaperture
+    int* obs_corner = nullptr;  // 4 halo-local corner indices packed in bytes: (r,c) (r,c+1) (r+1,c) (r+1,c+1)
+    int* halo_off = nullptr;    // [n_dom+1] into halo
+    int* halo = nullptr;        // valid-actuator indices of the corners of the observed subapertures
+    int* order = nullptr;       // [n_dom] processing order, most expensive first
+    // fused path: compressed observation operator per domain
+    int* rank = nullptr;        // [n_dom] rank r of the domain's Fried operator
+    int* fac_off = nullptr;     // [n_dom] float offset of [F^T (r x n_h) ; Q^T (r x p_loc)]
+    float* fac = nullptr;
+};
+
+// Host copy of the geometry and domains.
+struct HostModel {
+    int n_sub = 0;
+    std::vector<uint8_t> sub_valid, act_valid;
+    std::vector<int> sub_index, act_index;   // grid -> valid index or -1
+    std::vector<int> sub_rc, act_rc;         // valid index -> (r, c)
+    int n_act = 0, n_subv = 0;
+    std::vector<int> own_off, own, obs_off, obs_sub, obs_corner, halo_off, halo, order;
+    std::vector<int> rank, fac_off;
+    std::vector<float> fac;
+    int n_loc_max = 0, p_loc_max = 0, n_h_max = 0, rank_max = 0;
+};
+
+}  // namespace letkf
+
+struct letkf_ctx {
+    // parameters
+    int n_sub = 0, m = 0, m_pad = 0, mb_pad = 0, dom_sub = 0, halo = 0;
+    int precision = 0, path = 0, obs_block = 1, device = 0;
+    double a = 0, sigma = 0, q_white = 0;
+    unsigned long long seed = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    // geometry
+    letkf::HostModel host;
+    int n_act = 0, n_subv = 0, n = 0, p = 0, n_dom = 0;
+    letkf::DomainTables tab;
+    // ensemble: X[cur] is the current state, X[cur ^ 1] the next one (rows of m_pad elements)
+    void* X[2] = {nullptr, nullptr};
+    int cur = 0;
+    int phase = 0;                  // 0: forecast phase, 1: analysis phase
+    unsigned long long frame = 0;
+    // process noise
+    void* Lq = nullptr;             // device L in the GEMM input type, n_act x n_act row-major
+    void* Xi = nullptr;             // normals, n_act x (mb_pad or m_pad)
+    void* V = nullptr;              // perturbations, n_act x m_pad (state type)
+    cublasHandle_t cublas = nullptr;
+    // scratch of the plain path
+    void* S = nullptr;              // observed anomalies / sigma, sum(p_loc) x m_pad
+    void* dt = nullptr;             // innovations / sigma, sum(p_loc)
+    void* G = nullptr;              // n_dom x m x m_pad Gram matrices
+    void* b = nullptr;              // n_dom x m_pad
+    void* W = nullptr;              // n_dom x m x m_pad transforms w_bar 1^T + T
+    int* so_off = nullptr;          // [n_dom] slope row offset of each domain in S
+    int total_slopes = 0;
+    // device flags
+    int* d_status = nullptr;        // latched status bits
+    int* d_frame_bad = nullptr;     // current frame rejected
+    int* d_queue = nullptr;         // work-queue counter of the fused kernel
+    size_t device_bytes = 0;
+    int fused_smem = 0;             // dynamic shared memory of the fused kernel
+    int fused_grid = 0;
+    // stage timing
+    int prof_on = 0;
+    std::vector<int> prof_stage;            // stage of each record
+    std::vector<cudaEvent_t> prof_ev;       // two events per record
+    size_t prof_used = 0;
+};
+
+namespace letkf {
+
+int state_bytes(const letkf_ctx* c);
+
+enum Stage { STAGE_CHECK = 0, STAGE_NOISE = 1, STAGE_OBS = 2, STAGE_GRAM = 3, STAGE_EIG = 4,
+             STAGE_TRANSFORM = 5, STAGE_FORECAST = 6, STAGE_FUSED = 7 };
+// Record the start / end of a stage on the context's stream (no-ops unless profiling).
+void prof_begin(letkf_ctx* c, int stage);
+void prof_end(letkf_ctx* c);
+
+// plain.cu
+int plain_analyze(letkf_ctx* c, const void* y, double sigma);
+int plain_limits_ok(int precision, int m);
+size_t plain_smem_bytes(const letkf_ctx* c, int which);
+
+// misc.cu
+int launch_precheck(letkf_ctx* c, const void* y);
+int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis);
+int draw_perturbations(letkf_ctx* c, unsigned long long frame);
+int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host);
+int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
+
+// fused.cu
+int fused_prepare(letkf_ctx* c);
+int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast);
+
+}  // namespace letkf

@@ -1,0 +1,348 @@
+// Frame ingest check, process-noise draws, AR(1) forecast and initial ensemble.
+//
+// Forecast (Sect. 2.1): A1 = [[a I, 0], [I, 0]] on the two-instant state, so per
+// member: second instant <- first, first <- a * first + v.  The perturbation is
+// v = L xi with xi counter-based Philox4x32-10 normals (stream 1, frame k); with
+// a dense L the product is one GEMM per frame (cuBLAS: FP64 / FP32 / BF16 inputs
+// with FP32 accumulation, by precision), with white noise it is drawn inline.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace letkf {
+namespace {
+
+// Slope check of a frame: any NaN/Inf rejects the frame.  Also resets the work-queue counter
+// of the fused kernel that follows in stream order.
+template <typename T>
+__global__ void precheck_kernel(const T* __restrict__ y, int p, int* frame_bad, int* status, int* queue) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) {
+        bad = 0;
+        queue[0] = 0;
+    }
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+        if (!finite_val(y[i])) mine = 1;
+    if (mine) atomicOr(&bad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *frame_bad = bad;
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// xi[j, i] for j < n_act, i < m: one Philox call gives four consecutive j.
+template <typename O>
+__global__ void normals_kernel(O* __restrict__ out, int ld, int n_act, int m, unsigned long long seed,
+                               uint32_t stream, uint32_t frame) {
+    const int nq = (n_act + 3) / 4;
+    const int total = nq * m;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int q = t / m, i = t - q * m;
+        float zf[4];
+        double zd[4];
+        if (sizeof(O) == 8) {
+            normals4<double>(seed, stream, frame, (uint32_t)i, (uint32_t)q, zd);
+        } else {
+            normals4<float>(seed, stream, frame, (uint32_t)i, (uint32_t)q, zf);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int j = 4 * q + r;
+            if (j < n_act) {
+                if (sizeof(O) == 8)
+                    out[(size_t)j * ld + i] = (O)zd[r];
+                else
+                    out[(size_t)j * ld + i] = (O)zf[r];
+            }
+        }
+    }
+}
+
+// In-place forecast of the ensemble X (n x m_pad) and the mean of the new first instant.
+// vmode 0: v from V (ld vld); 1: white noise q * xi drawn inline; 2: no perturbation.
+template <typename T>
+__global__ void forecast_kernel(T* __restrict__ X, const T* __restrict__ V, int vld, int vmode, T q_white,
+                                T a, int n_act, int m, int m_pad, T* __restrict__ xpred,
+                                const int* __restrict__ frame_bad, int check_bad, unsigned long long seed,
+                                uint32_t frame) {
+    const bool skip = check_bad && *frame_bad;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n_act; j += warps) {
+        T* x1 = X + (size_t)j * m_pad;
+        T* x2 = X + (size_t)(n_act + j) * m_pad;
+        T s = 0;
+        for (int i = lane; i < m; i += 32) {
+            T v1 = x1[i];
+            if (!skip) {
+                T v = 0;
+                if (vmode == 0) {
+                    v = V[(size_t)j * vld + i];
+                } else if (vmode == 1) {
+                    T z[4];
+                    normals4<T>(seed, 1u, frame, (uint32_t)i, (uint32_t)(j >> 2), z);
+                    v = q_white * z[j & 3];
+                }
+                x2[i] = v1;
+                v1 = a * v1 + v;
+                x1[i] = v1;
+            }
+            s += v1;
+        }
+        s = warp_sum(s);
+        if (xpred && lane == 0) xpred[j] = s / (T)m;
+    }
+}
+
+template <typename T>
+__global__ void axpy_rows_kernel(T* __restrict__ dst, const T* __restrict__ src, T alpha, T beta, int rows,
+                                 int cols, int ld) {
+    // dst = alpha * dst + beta * src (rows x cols, leading dimension ld)
+    const size_t total = (size_t)rows * cols;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = t / cols, cidx = t - r * cols;
+        dst[r * ld + cidx] = alpha * dst[r * ld + cidx] + beta * src[r * ld + cidx];
+    }
+}
+
+__global__ void f64_to_f32(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        out[t] = (float)in[t];
+}
+
+__global__ void f64_to_bf16(const double* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        out[t] = __float2bfloat16_rn((float)in[t]);
+}
+
+int grid_for(size_t work, int block) {
+    size_t g = (work + block - 1) / block;
+    if (g > 8192) g = 8192;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// V (n_act x m, ld m_pad) = L (n_act x n_act, row-major) * Xi (n_act x m, ld xld).
+// Column-major view used by cuBLAS: V^T = Xi^T L^T.
+int noise_gemm(letkf_ctx* c, const void* L, const void* Xi, int xld, int gemm_type, void* V) {
+    const int m = c->m, na = c->n_act;
+    cublasStatus_t st;
+    if (gemm_type == 0) {
+        const double one = 1.0, zero = 0.0;
+        st = cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, (const double*)Xi, xld,
+                         (const double*)L, na, &zero, (double*)V, c->m_pad);
+    } else if (gemm_type == 1) {
+        const float one = 1.f, zero = 0.f;
+        st = cublasSgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, (const float*)Xi, xld,
+                         (const float*)L, na, &zero, (float*)V, c->m_pad);
+    } else {
+        const float one = 1.f, zero = 0.f;
+        st = cublasGemmEx(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, Xi, CUDA_R_16BF, xld, L,
+                          CUDA_R_16BF, na, &zero, V, CUDA_R_32F, c->m_pad, CUBLAS_COMPUTE_32F,
+                          CUBLAS_GEMM_DEFAULT);
+    }
+    return st == CUBLAS_STATUS_SUCCESS ? LETKF_OK : LETKF_ECUDA;
+}
+
+int gemm_type_of(const letkf_ctx* c) {
+    return c->precision == LETKF_PREC_FP64 ? 0 : (c->precision == LETKF_PREC_FP32 ? 1 : 2);
+}
+
+}  // namespace
+
+int draw_perturbations_impl(letkf_ctx* c, unsigned long long frame);
+
+int launch_precheck(letkf_ctx* c, const void* y) {
+    prof_begin(c, STAGE_CHECK);
+    if (c->precision == LETKF_PREC_FP64)
+        precheck_kernel<double><<<1, 1024, 0, c->stream>>>((const double*)y, c->p, c->d_frame_bad, c->d_status,
+                                                            c->d_queue);
+    else
+        precheck_kernel<float><<<1, 1024, 0, c->stream>>>((const float*)y, c->p, c->d_frame_bad, c->d_status,
+                                                           c->d_queue);
+    prof_end(c);
+    return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
+}
+
+int draw_perturbations(letkf_ctx* c, unsigned long long frame) {
+    prof_begin(c, STAGE_NOISE);
+    const int rc = draw_perturbations_impl(c, frame);
+    prof_end(c);
+    return rc;
+}
+
+int draw_perturbations_impl(letkf_ctx* c, unsigned long long frame) {
+    const int gt = gemm_type_of(c);
+    const int nq = (c->n_act + 3) / 4;
+    const int g = grid_for((size_t)nq * c->m, 256);
+    if (gt == 0)
+        normals_kernel<double><<<g, 256, 0, c->stream>>>((double*)c->Xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
+                                                         (uint32_t)frame);
+    else if (gt == 1)
+        normals_kernel<float><<<g, 256, 0, c->stream>>>((float*)c->Xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
+                                                        (uint32_t)frame);
+    else
+        normals_kernel<__nv_bfloat16><<<g, 256, 0, c->stream>>>((__nv_bfloat16*)c->Xi, c->mb_pad, c->n_act, c->m,
+                                                                c->seed, 1u, (uint32_t)frame);
+    if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
+    return noise_gemm(c, c->Lq, c->Xi, gt == 2 ? c->mb_pad : c->m_pad, gt, c->V);
+}
+
+int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis) {
+    int vmode, vld;
+    const void* Vp;
+    if (v_user) {
+        vmode = 0;
+        Vp = v_user;
+        vld = c->m;
+    } else if (c->Lq) {
+        int rc = draw_perturbations(c, c->frame);
+        if (rc) return rc;
+        vmode = 0;
+        Vp = c->V;
+        vld = c->m_pad;
+    } else {
+        vmode = c->q_white > 0 ? 1 : 2;
+        Vp = nullptr;
+        vld = 0;
+    }
+    const int g = grid_for((size_t)c->n_act * 32, 256);
+    prof_begin(c, STAGE_FORECAST);
+    if (c->precision == LETKF_PREC_FP64)
+        forecast_kernel<double><<<g, 256, 0, c->stream>>>((double*)c->X[c->cur], (const double*)Vp, vld, vmode,
+                                                          c->q_white, c->a, c->n_act, c->m, c->m_pad,
+                                                          (double*)xpred, c->d_frame_bad, in_analysis, c->seed,
+                                                          (uint32_t)c->frame);
+    else
+        forecast_kernel<float><<<g, 256, 0, c->stream>>>((float*)c->X[c->cur], (const float*)Vp, vld, vmode,
+                                                         (float)c->q_white, (float)c->a, c->n_act, c->m, c->m_pad,
+                                                         (float*)xpred, c->d_frame_bad, in_analysis, c->seed,
+                                                         (uint32_t)c->frame);
+    prof_end(c);
+    return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
+}
+
+// Initial ensemble (Sect. 2.2): second instant = P0 xi0, first = a * second + L xi1, with
+// xi0, xi1 the Philox draws (stream 0, frames 0 and 1).  P0 defaults to L / sqrt(1 - a^2).
+int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
+    const int na = c->n_act, m = c->m;
+    const bool f64 = c->precision == LETKF_PREC_FP64;
+    const size_t eb = f64 ? 8 : 4;
+    const size_t nn = (size_t)na * na;
+    const size_t row = (size_t)c->m_pad * eb;
+    // buffers for the process-noise draws of later frames
+    if (L_host) {
+        void* tmp = nullptr;
+        if (cudaMalloc(&tmp, nn * 8) != cudaSuccess) return LETKF_ENOMEM;
+        cudaMemcpy(tmp, L_host, nn * 8, cudaMemcpyHostToDevice);
+        const size_t lbytes = c->precision == LETKF_PREC_MIXED ? nn * 2 : nn * eb;
+        if (cudaMalloc(&c->Lq, lbytes) != cudaSuccess) { cudaFree(tmp); return LETKF_ENOMEM; }
+        c->device_bytes += lbytes;
+        const int g = grid_for(nn, 256);
+        if (f64)
+            cudaMemcpyAsync(c->Lq, tmp, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+        else if (c->precision == LETKF_PREC_FP32)
+            f64_to_f32<<<g, 256, 0, c->stream>>>((const double*)tmp, (float*)c->Lq, nn);
+        else
+            f64_to_bf16<<<g, 256, 0, c->stream>>>((const double*)tmp, (__nv_bfloat16*)c->Lq, nn);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        const size_t xib = c->precision == LETKF_PREC_MIXED ? (size_t)na * c->mb_pad * 2 : (size_t)na * row;
+        if (cudaMalloc(&c->Xi, xib) != cudaSuccess) return LETKF_ENOMEM;
+        cudaMemset(c->Xi, 0, xib);
+        c->device_bytes += xib;
+    }
+    // the initial ensemble itself is formed at full state precision (FP64 or FP32 GEMMs)
+    const int gt = f64 ? 0 : 1;
+    void *Lf = nullptr, *Pf = nullptr, *xi = nullptr;
+    const size_t fb = f64 ? 8 : 4;
+    auto upload_conv = [&](const double* src, double scale, void** dst) -> int {
+        void* tmp = nullptr;
+        if (cudaMalloc(&tmp, nn * 8) != cudaSuccess) return LETKF_ENOMEM;
+        std::vector<double> h(src, src + nn);
+        if (scale != 1.0)
+            for (auto& v : h) v *= scale;
+        cudaMemcpy(tmp, h.data(), nn * 8, cudaMemcpyHostToDevice);
+        if (cudaMalloc(dst, nn * fb) != cudaSuccess) { cudaFree(tmp); return LETKF_ENOMEM; }
+        if (f64)
+            cudaMemcpy(*dst, tmp, nn * 8, cudaMemcpyDeviceToDevice);
+        else
+            f64_to_f32<<<grid_for(nn, 256), 256, 0, c->stream>>>((const double*)tmp, (float*)*dst, nn);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        return LETKF_OK;
+    };
+    int rc = LETKF_OK;
+    if (cudaMalloc(&xi, (size_t)na * row) != cudaSuccess) return LETKF_ENOMEM;
+    cudaMemset(xi, 0, (size_t)na * row);
+    const double sa = 1.0 / std::sqrt(1.0 - c->a * c->a);
+    void* X = c->X[0];
+    void* X2 = static_cast<char*>(X) + (size_t)na * row;  // second instant rows
+    const int nq = (na + 3) / 4;
+    const int g = grid_for((size_t)nq * m, 256);
+    auto draw = [&](uint32_t frame) {
+        if (f64)
+            normals_kernel<double><<<g, 256, 0, c->stream>>>((double*)xi, c->m_pad, na, m, c->seed, 0u, frame);
+        else
+            normals_kernel<float><<<g, 256, 0, c->stream>>>((float*)xi, c->m_pad, na, m, c->seed, 0u, frame);
+    };
+    if (L_host) {
+        if ((rc = upload_conv(L_host, 1.0, &Lf))) goto done;
+        if (P0_host) {
+            if ((rc = upload_conv(P0_host, 1.0, &Pf))) goto done;
+        } else {
+            if ((rc = upload_conv(L_host, sa, &Pf))) goto done;
+        }
+        draw(0);
+        if ((rc = noise_gemm(c, Pf, xi, c->m_pad, gt, X2))) goto done;
+        draw(1);
+        if ((rc = noise_gemm(c, Lf, xi, c->m_pad, gt, X))) goto done;  // first rows <- L xi1
+    } else {
+        // white noise: second = (q / sqrt(1 - a^2)) xi0 (or P0 xi0), first = a second + q xi1
+        if (P0_host) {
+            if ((rc = upload_conv(P0_host, 1.0, &Pf))) goto done;
+            draw(0);
+            if ((rc = noise_gemm(c, Pf, xi, c->m_pad, gt, X2))) goto done;
+        } else {
+            draw(0);
+            cudaMemcpyAsync(X2, xi, (size_t)na * row, cudaMemcpyDeviceToDevice, c->stream);
+            if (f64)
+                axpy_rows_kernel<double><<<grid_for((size_t)na * m, 256), 256, 0, c->stream>>>(
+                    (double*)X2, (const double*)xi, 0.0, c->q_white * sa, na, m, c->m_pad);
+            else
+                axpy_rows_kernel<float><<<grid_for((size_t)na * m, 256), 256, 0, c->stream>>>(
+                    (float*)X2, (const float*)xi, 0.f, (float)(c->q_white * sa), na, m, c->m_pad);
+        }
+        draw(1);
+        if (f64)
+            axpy_rows_kernel<double><<<grid_for((size_t)na * m, 256), 256, 0, c->stream>>>(
+                (double*)X, (const double*)xi, 0.0, c->q_white, na, m, c->m_pad);
+        else
+            axpy_rows_kernel<float><<<grid_for((size_t)na * m, 256), 256, 0, c->stream>>>(
+                (float*)X, (const float*)xi, 0.f, (float)c->q_white, na, m, c->m_pad);
+    }
+    // first += a * second
+    if (f64)
+        axpy_rows_kernel<double><<<grid_for((size_t)na * m, 256), 256, 0, c->stream>>>(
+            (double*)X, (const double*)X2, 1.0, c->a, na, m, c->m_pad);
+    else
+        axpy_rows_kernel<float><<<grid_for((size_t)na * m, 256), 256, 0, c->stream>>>(
+            (float*)X, (const float*)X2, 1.f, (float)c->a, na, m, c->m_pad);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = LETKF_ECUDA;
+done:
+    cudaStreamSynchronize(c->stream);
+    if (Lf) cudaFree(Lf);
+    if (Pf) cudaFree(Pf);
+    if (xi) cudaFree(xi);
+    return rc;
+}
+
+}  // namespace letkf

@@ -1,0 +1,124 @@
+"""A context object over the C ABI that takes torch device tensors.
+
+All arithmetic happens in libletkf's kernels; this class only allocates output
+tensors with torch, checks shapes and dtypes, and passes raw pointers and the
+current torch stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+
+_PREC = {"fp64": _lib.LETKF_PREC_FP64, "fp32": _lib.LETKF_PREC_FP32, "mixed": _lib.LETKF_PREC_MIXED}
+_PATH = {"plain": _lib.LETKF_PATH_PLAIN, "fused": _lib.LETKF_PATH_FUSED}
+
+
+class LETKF:
+    """One adaptive-optics system's local ETKF, resident on one GPU."""
+
+    def __init__(self, n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4, halo: int = 2,
+                 obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
+                 q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0,
+                 p0_sqrt: Optional[np.ndarray] = None, precision: str = "fp32", path: str = "plain",
+                 seed: int = 0, obs_block: int = 1, device: Optional[int] = None, stream=None):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("LETKF needs a CUDA device")
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = torch.device("cuda", dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p = _lib.letkf_params()
+        p.n_sub = int(n_sub)
+        self._keep = []
+        if sub_valid is not None:
+            sv = np.ascontiguousarray(sub_valid, dtype=np.uint8)
+            self._keep.append(sv)
+            p.sub_valid = sv.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        p.obstruction = float(obstruction)
+        p.ar1_a = float(ar1_a)
+        p.obs_block = int(obs_block)
+        if q_sqrt is not None:
+            qs = np.ascontiguousarray(q_sqrt, dtype=np.float64)
+            self._keep.append(qs)
+            p.q_sqrt = qs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.q_white = float(q_white)
+        if p0_sqrt is not None:
+            ps = np.ascontiguousarray(p0_sqrt, dtype=np.float64)
+            self._keep.append(ps)
+            p.p0_sqrt = ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.sigma = float(sigma)
+        p.m = int(m)
+        p.dom_sub = int(dom_sub)
+        p.halo = int(halo)
+        p.precision = _PREC[precision]
+        p.path = _PATH[path]
+        p.seed = int(seed)
+        p.device = dev
+        p.stream = self.stream.cuda_stream
+        with torch.cuda.device(self.device):
+            self.ctx = _lib.letkf_create(p)
+        self._keep = []
+        self.info = _lib.letkf_get_info(self.ctx)
+        self.dtype = torch.float64 if self.info.state_bytes == 8 else torch.float32
+        self.precision, self.path = precision, path
+
+    # --- geometry -------------------------------------------------------------------
+    def geometry(self):
+        n = self.info.n_sub
+        sv = np.zeros((n, n), dtype=np.uint8)
+        av = np.zeros((n + 1, n + 1), dtype=np.uint8)
+        _lib.letkf_get_geometry(self.ctx, sv.ctypes.data, av.ctypes.data)
+        return sv.astype(bool), av.astype(bool)
+
+    # --- filter ---------------------------------------------------------------------
+    def _dev(self, t, n, name):
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} tensor of {n} elements on {self.device}")
+        return t.data_ptr()
+
+    def analyze(self, y, sigma: float = 0.0) -> None:
+        _lib.letkf_analyze(self.ctx, self._dev(y, self.info.p, "y"), sigma)
+
+    def forecast(self, v=None) -> None:
+        ptr = 0 if v is None else self._dev(v, self.info.n_act * self.info.m, "v")
+        _lib.letkf_forecast(self.ctx, ptr)
+
+    def step(self, y, sigma: float = 0.0, out=None):
+        """One frame (Eq. 1 order): analysis with y, forecast; returns x_hat(k+1|k) (n_act)."""
+        if out is None:
+            out = self._torch.empty(self.info.n_act, dtype=self.dtype, device=self.device)
+        _lib.letkf_step(self.ctx, self._dev(y, self.info.p, "y"), sigma, self._dev(out, self.info.n_act, "out"))
+        return out
+
+    def get_state(self, out=None):
+        if out is None:
+            out = self._torch.empty((self.info.n, self.info.m), dtype=self.dtype, device=self.device)
+        frame = _lib.letkf_get_state(self.ctx, self._dev(out, self.info.n * self.info.m, "x"))
+        return out, frame
+
+    def set_state(self, x, frame: int) -> None:
+        _lib.letkf_set_state(self.ctx, self._dev(x, self.info.n * self.info.m, "x"), frame)
+
+    def profile(self, enable: bool):
+        """Start (True) or stop (False) stage timing; stopping returns {stage: (ms, launches)}."""
+        return _lib.letkf_profile(self.ctx, 1 if enable else 0)
+
+    def sync(self) -> int:
+        return _lib.letkf_sync(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            _lib.letkf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,54 @@
+"""Shared set-up of the GPU parity tests: one workload, seen by the CUDA path and by the oracle.
+
+Both sides get the same seeded inputs from `synth` (slopes, process-noise and
+stationary covariance factors) and the same Philox seed; each side builds its
+own geometry and draws its own normals.
+"""
+
+import functools
+
+import numpy as np
+
+from oracle import etkf, geometry
+from synth import TruthStream, workload
+
+
+@functools.lru_cache(maxsize=None)
+def model(name, m=None, **over):
+    w = workload(name)
+    for k, v in over.items():
+        setattr(w, k, v)
+    if m is not None:
+        w.m = m
+    g = geometry.make_geometry(w.n_sub, w.obstruction)
+    doms = geometry.make_domains(g, w.dom_sub, w.halo)
+    L = w.process_noise_sqrt(g.act_rc)
+    Ls = w.stationary_sqrt(g.act_rc)
+    return w, g, doms, L, Ls
+
+
+@functools.lru_cache(maxsize=None)
+def slopes(name, n_frames, **over):
+    w, g, _, _, _ = model(name, **over)
+    fr = TruthStream(w).frames(0, n_frames + 1)
+    y = np.concatenate([fr["slopes"][:, 0][:, g.sub_valid], fr["slopes"][:, 1][:, g.sub_valid]], axis=1)
+    return y, fr["phi_act"][:, g.act_valid]
+
+
+def oracle_filter(name, m=None, **over):
+    w, g, doms, L, Ls = model(name, m, **over)
+    return etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls, obs_block=w.obs_block)
+
+
+def gpu_filter(name, precision, path, m=None, **over):
+    from paper_1310_5954_gb300 import LETKF
+    w, g, doms, L, Ls = model(name, m, **over)
+    return LETKF(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
+                 obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=precision, path=path,
+                 seed=w.seed, obs_block=w.obs_block)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
