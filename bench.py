@@ -114,7 +114,7 @@ def workload_inputs(wname, n_frames, sub_valid, act_valid):
     from synth import TruthStream, workload
     w = workload(wname)
     fr = TruthStream(w).frames(0, n_frames + 1)
-    y = np.concatenate([fr["slopes"][:, 0][:, sub_valid], fr["slopes"][:, 1][:, sub_valid]], axis=1)
+    y = np.ascontiguousarray(np.concatenate([fr["slopes"][:, 0][:, sub_valid], fr["slopes"][:, 1][:, sub_valid]], axis=1))
     phi = fr["phi_act"][:, act_valid]
     return w, y, phi
 

@@ -79,7 +79,8 @@ class LETKF:
     # --- filter ---------------------------------------------------------------------
     def _dev(self, t, n, name):
         if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != n:
-            raise ValueError(f"{name}: expected a contiguous {self.dtype} tensor of {n} elements on {self.device}")
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} tensor of {n} elements on {self.device}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device} (contiguous: {t.is_contiguous()})")
         return t.data_ptr()
 
     def analyze(self, y, sigma: float = 0.0) -> None:

@@ -32,7 +32,7 @@ def slopes(name, n_frames, **over):
     w, g, _, _, _ = model(name, **over)
     fr = TruthStream(w).frames(0, n_frames + 1)
     y = np.concatenate([fr["slopes"][:, 0][:, g.sub_valid], fr["slopes"][:, 1][:, g.sub_valid]], axis=1)
-    return y, fr["phi_act"][:, g.act_valid]
+    return np.ascontiguousarray(y), np.ascontiguousarray(fr["phi_act"][:, g.act_valid])
 
 
 def oracle_filter(name, m=None, **over):
