@@ -109,6 +109,9 @@ typedef struct letkf_info {
     int precision, path;
     unsigned long long frame;       /* frames forecast so far */
     size_t device_bytes;            /* device memory held by the context */
+    int n_domains_observing;        /* domains with at least one observed subaperture */
+    long long sum_p_loc;            /* total slopes over domains (each counted once per domain) */
+    long long sum_n_loc;            /* total state rows over domains (= n) */
 } letkf_info;
 
 /*

@@ -48,7 +48,8 @@ class letkf_info(ctypes.Structure):
         ("p", ctypes.c_int), ("m", ctypes.c_int), ("n_domains", ctypes.c_int), ("n_loc_max", ctypes.c_int),
         ("p_loc_max", ctypes.c_int), ("rank_max", ctypes.c_int), ("state_bytes", ctypes.c_int),
         ("precision", ctypes.c_int), ("path", ctypes.c_int), ("frame", ctypes.c_ulonglong),
-        ("device_bytes", ctypes.c_size_t),
+        ("device_bytes", ctypes.c_size_t), ("n_domains_observing", ctypes.c_int),
+        ("sum_p_loc", ctypes.c_longlong), ("sum_n_loc", ctypes.c_longlong),
     ]
 
 

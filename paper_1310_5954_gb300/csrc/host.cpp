@@ -436,6 +436,15 @@ int letkf_get_info(const letkf_ctx* c, letkf_info* o) {
     o->n_domains = c->n_dom; o->n_loc_max = c->host.n_loc_max; o->p_loc_max = c->host.p_loc_max;
     o->rank_max = c->host.rank_max; o->state_bytes = letkf::state_bytes(c);
     o->precision = c->precision; o->path = c->path; o->frame = c->frame; o->device_bytes = c->device_bytes;
+    o->n_domains_observing = 0;
+    o->sum_p_loc = 0;
+    o->sum_n_loc = 0;
+    for (int d = 0; d < c->n_dom; ++d) {
+        const int no = c->host.obs_off[d + 1] - c->host.obs_off[d];
+        if (no > 0) o->n_domains_observing += 1;
+        o->sum_p_loc += 2 * no;
+        o->sum_n_loc += 2 * (c->host.own_off[d + 1] - c->host.own_off[d]);
+    }
     return LETKF_OK;
 }
 
