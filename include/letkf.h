@@ -56,7 +56,8 @@ typedef enum letkf_status {
     LETKF_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
     LETKF_ENONFINITE = -5,  /* non-finite slopes: that frame was rejected, state unchanged */
     LETKF_ESTATE = -6,      /* call out of order (e.g. analyze twice without a forecast) */
-    LETKF_ENOCONV = -7      /* a domain eigensolve hit its sweep limit (result still written) */
+    LETKF_ENOCONV = -7,     /* a domain eigensolve hit its sweep limit (result still written) */
+    LETKF_ESCRATCH = -8     /* the problem does not fit letkf_analyze_static's fixed scratch */
 } letkf_status;
 
 typedef enum letkf_precision {
@@ -170,6 +171,30 @@ int letkf_set_state(letkf_ctx* ctx, const void* x_dev, unsigned long long frame)
 
 /* Wait for the context's queued work and return the first latched device error, clearing it. */
 int letkf_sync(letkf_ctx* ctx);
+
+/*
+ * letkf_analyze_static: the analysis of letkf_analyze (plain path, Sect. 2.3) without any
+ * allocation, for callers that cannot call the CUDA allocator while they run, e.g. a real-time
+ * controller that reserves its device memory before its loop and must not block on or fail in
+ * an allocation with a frame deadline pending.  The paper has no counterpart.
+ *
+ * Reads the context's current forecast ensemble and the slopes y_dev (p elements, state type),
+ * and writes the analysis ensemble to xa_dev (n x m, state type, caller-owned).  It leaves the
+ * context's ensemble, phase and frame counter untouched; a non-finite slope makes xa_dev a
+ * copy of the forecast and latches LETKF_ENONFINITE for letkf_sync.  sigma > 0 is used for
+ * this call only.
+ *
+ * All intermediate storage comes from one fixed 16 MiB array per GPU that exists while the
+ * library is loaded (every GPU that loads the library holds it).  A problem needing more
+ * returns LETKF_ESCRATCH before any work is queued (the ELT-class 80x80, m = 100 system needs
+ * ~43 MiB; the 8x8 and 40x40 systems fit).  Every call shares that array and it keeps the last
+ * call's contents: calls whose work may overlap on the device (other streams, other contexts
+ * on the same GPU) race and must be serialised by the caller.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Plain-path contexts only (LETKF_EINVAL otherwise); requires the forecast phase
+ * (LETKF_ESTATE).
+ */
+int letkf_analyze_static(letkf_ctx* ctx, const void* y_dev, double sigma, void* xa_dev);
 
 /* Static English description of a status code. */
 const char* letkf_status_string(int status);

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libletkf.so")
 
 LETKF_OK, LETKF_EINVAL, LETKF_ENOMEM, LETKF_ECUDA = 0, -1, -2, -3
 LETKF_ETIMEOUT, LETKF_ENONFINITE, LETKF_ESTATE, LETKF_ENOCONV = -4, -5, -6, -7
+LETKF_ESCRATCH = -8
 LETKF_PREC_FP64, LETKF_PREC_FP32, LETKF_PREC_MIXED = 0, 1, 2
 LETKF_PATH_PLAIN, LETKF_PATH_FUSED = 0, 1
 
@@ -72,6 +73,7 @@ _SIGS = {
     "letkf_get_state": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_ulonglong)]),
     "letkf_set_state": (ctypes.c_int, [_VP, _VP, ctypes.c_ulonglong]),
     "letkf_sync": (ctypes.c_int, [_VP]),
+    "letkf_analyze_static": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP]),
     "letkf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "letkf_profile": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "letkf_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
@@ -155,6 +157,11 @@ def letkf_get_state(ctx: int, x_ptr: int = 0) -> int:
 
 def letkf_set_state(ctx: int, x_ptr: int, frame: int) -> int:
     return _check(load().letkf_set_state(ctx, x_ptr, int(frame)), "letkf_set_state")
+
+
+def letkf_analyze_static(ctx: int, y_ptr: int, sigma: float, xa_ptr: int) -> int:
+    """Allocation-free analysis into the caller's buffer; returns the status code (no raise)."""
+    return load().letkf_analyze_static(ctx, y_ptr, float(sigma), xa_ptr)
 
 
 def letkf_sync(ctx: int) -> int:

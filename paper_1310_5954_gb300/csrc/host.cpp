@@ -583,6 +583,7 @@ const char* letkf_status_string(int s) {
         case LETKF_ENONFINITE: return "non-finite slopes: frame rejected, state unchanged";
         case LETKF_ESTATE: return "call out of order";
         case LETKF_ENOCONV: return "an eigensolve reached its sweep limit";
+        case LETKF_ESCRATCH: return "problem too large for the fixed 16 MiB scratch of letkf_analyze_static";
         default: return "unknown status";
     }
 }

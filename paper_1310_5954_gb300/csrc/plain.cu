@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.hpp"
@@ -430,3 +431,119 @@ int plain_analyze(letkf_ctx* c, const void* y, double sigma) {
 }
 
 }  // namespace letkf
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free analysis.
+//
+// Some callers cannot call the CUDA allocator while they run the filter: a real-time
+// controller typically reserves all of its device memory before its loop starts, and an
+// allocation inside the loop may block on the driver or fail under fragmentation while a
+// frame deadline is pending.  letkf_analyze_static serves them: it runs the same plain-path
+// kernels as letkf_analyze but takes all of its intermediate storage from one fixed array
+// that exists for as long as the library is loaded, and it allocates nothing.
+namespace letkf {
+namespace {
+
+// 16 MiB of scratch per GPU, held by every GPU that loads the library until the process
+// exits.  Shared by every call on that GPU: calls whose work overlaps on the device race on it.
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device ordinal (in host code the array's name is
+// only a stand-in for it), found once per device with that device current.
+std::mutex g_static_mutex;
+void* g_static_ptr[64] = {nullptr};
+
+int static_scratch_address(int device, void** out) {
+    if (device < 0 || device >= 64) return LETKF_EINVAL;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return LETKF_ECUDA;
+        g_static_ptr[device] = p;
+    }
+    *out = g_static_ptr[device];
+    return LETKF_OK;
+}
+
+// Slope check of the allocation-free path: writes its own reject flag (never the context's).
+template <typename T>
+__global__ void static_check_kernel(const T* __restrict__ y, int p, int* flag, int* status) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+        if (!finite_val(y[i])) mine = 1;
+    if (mine) atomicOr(&bad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *flag = bad;
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+template <typename T>
+int analyze_static_t(letkf_ctx* c, const T* y, double sigma, T* out) {
+    const int m = c->m, mp = c->m_pad, nd = c->n_dom;
+    const size_t eb = sizeof(T);
+    // carve the scratch: slopes, innovations, Gram, b, weights, the analysis rows, the flag
+    const size_t o_S = 0;
+    const size_t o_dt = align256(o_S + (size_t)std::max(c->total_slopes, 1) * mp * eb);
+    const size_t o_G = align256(o_dt + (size_t)std::max(c->total_slopes, 1) * eb);
+    const size_t o_b = align256(o_G + (size_t)nd * m * mp * eb);
+    const size_t o_W = align256(o_b + (size_t)nd * mp * eb);
+    const size_t o_X = align256(o_W + (size_t)nd * m * mp * eb);
+    const size_t o_flag = align256(o_X + (size_t)c->n * mp * eb);
+    const size_t need = o_flag + 256;
+    if (need > kStaticScratchBytes) return LETKF_ESCRATCH;
+    void* base = nullptr;
+    int rc = static_scratch_address(c->device, &base);
+    if (rc) return rc;
+    unsigned char* sb = static_cast<unsigned char*>(base);
+    T* S = reinterpret_cast<T*>(sb + o_S);
+    T* dt = reinterpret_cast<T*>(sb + o_dt);
+    T* G = reinterpret_cast<T*>(sb + o_G);
+    T* bv = reinterpret_cast<T*>(sb + o_b);
+    T* W = reinterpret_cast<T*>(sb + o_W);
+    T* Xo = reinterpret_cast<T*>(sb + o_X);
+    int* flag = reinterpret_cast<int*>(sb + o_flag);
+    const T* X = static_cast<const T*>(c->X[c->cur]);
+    const double sg = sigma > 0 ? sigma : c->sigma;
+    const int row0 = c->obs_block == 1 ? c->n_act : 0;
+    const size_t sm_obs = (size_t)c->host.n_h_max * (m + 1) * sizeof(T);
+    const size_t sm_gram = (size_t)std::max(c->host.p_loc_max, 1) * (m + 1) * sizeof(T);
+    const int M = m + (m & 1);
+    const size_t sm_eig = (size_t)2 * M * (M + 1) * sizeof(T) + (size_t)3 * M * sizeof(T) + (size_t)M * sizeof(int);
+    const size_t sm_tr = ((size_t)m * m + (size_t)c->host.n_loc_max * (m + 1)) * sizeof(T);
+    cudaFuncSetAttribute(plain_obs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_obs);
+    cudaFuncSetAttribute(plain_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram);
+    cudaFuncSetAttribute(plain_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_eig);
+    cudaFuncSetAttribute(plain_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tr);
+    static_check_kernel<T><<<1, 1024, 0, c->stream>>>(y, c->p, flag, c->d_status);
+    plain_obs<T><<<nd, kThreads, sm_obs, c->stream>>>(X, y, c->tab, c->so_off, S, dt, m, mp, row0, c->n_subv,
+                                                      (T)(1.0 / sg), flag);
+    plain_gram<T><<<nd, kThreads, sm_gram, c->stream>>>(S, dt, c->tab, c->so_off, G, bv, m, mp, flag);
+    plain_eig<T><<<nd, kEigThreads, sm_eig, c->stream>>>(G, bv, W, m, mp, c->d_status, flag);
+    plain_transform<T><<<nd, kThreads, sm_tr, c->stream>>>(X, Xo, W, c->tab, m, mp, c->n_act, flag);
+    if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
+    if (cudaMemcpy2DAsync(out, (size_t)m * eb, Xo, (size_t)mp * eb, (size_t)m * eb, c->n, cudaMemcpyDeviceToDevice,
+                          c->stream) != cudaSuccess)
+        return LETKF_ECUDA;
+    return LETKF_OK;
+}
+
+}  // namespace
+}  // namespace letkf
+
+extern "C" int letkf_analyze_static(letkf_ctx* c, const void* y_dev, double sigma, void* xa_dev) {
+    if (!c || !y_dev || !xa_dev) return LETKF_EINVAL;
+    if (c->path != LETKF_PATH_PLAIN) return LETKF_EINVAL;
+    if (c->phase != 0) return LETKF_ESTATE;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LETKF_ECUDA;
+    if (c->precision == LETKF_PREC_FP64)
+        return letkf::analyze_static_t<double>(c, static_cast<const double*>(y_dev), sigma, static_cast<double*>(xa_dev));
+    return letkf::analyze_static_t<float>(c, static_cast<const float*>(y_dev), sigma, static_cast<float*>(xa_dev));
+}

@@ -28,7 +28,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for s in range(-7, 1):
+    for s in range(-8, 1):
         assert _lib.letkf_status_string(s) not in ("", "unknown status")
     assert _lib.letkf_status_string(-99) == "unknown status"
 
