@@ -61,9 +61,9 @@ struct FusedArgs {
     float* xpred;
     DomainTables tab;
     int* status;
-    const int* frame_bad;
-    int* queue;
-    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP;
+    int* frame_bad;
+    int* queue;          // [0] next work item, [1] CTAs done (the last one resets both)
+    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, p;
     float inv_sigma, a, q_white;
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
@@ -260,7 +260,16 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
     const uint32_t tbase = ctl->tmem_base;
     const uint32_t tl = tbase + lane_off + (uint32_t)col0;   // this thread's lane, first column
     uint32_t ph_load = 0, ph_mma = 0;
-    const bool rejected = *A.frame_bad != 0;
+    // frame ingest: every CTA checks the whole slope vector, so all of them agree on
+    // rejecting a frame with a non-finite slope (the ensemble is then left unchanged)
+    int nonfinite = 0;
+    for (int i = tid; i < A.p; i += FT)
+        if (!isfinite(A.y[i])) nonfinite = 1;
+    const bool rejected = __syncthreads_or(nonfinite) != 0;
+    if (blockIdx.x == 0 && tid == 0) {
+        *A.frame_bad = rejected ? 1 : 0;
+        if (rejected) atomicOr(A.status, ST_NONFINITE);
+    }
 
     if (tid == 0) {
         const int it0 = atomicAdd(A.queue, 1);
@@ -656,6 +665,15 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
     }
     // a wait that ran out may leave bulk copies in flight: give them a bounded time to land
     if (ctl->abort && tid == 0) mbar_wait_bounded(&ctl->bar_load, ph_load, WAIT_CYCLES);
+    // the last CTA to finish resets the work queue for the next launch (all fetches are done)
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&A.queue[1], 1) == (int)gridDim.x - 1) {
+            A.queue[0] = 0;
+            A.queue[1] = 0;
+            __threadfence();
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -776,24 +794,70 @@ int fused_prepare(letkf_ctx* c) {
     c->fused_smem = L.total;
     if (cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
         return LETKF_ECUDA;
+    // One CTA per SM pulling domains from the work queue: domains differ in cost (edge domains
+    // see fewer subapertures), so the full grid balances better than fewer, evenly loaded CTAs.
     c->fused_grid = std::min(c->sms, c->n_dom);
+    // lowest priority: the side stream's blocks never take an SM that the frame's kernel is waiting for
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) return LETKF_ECUDA;
+    if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess) return LETKF_ECUDA;
+    if (cublasCreate(&c->cublas_side) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
+    if (cublasSetStream(c->cublas_side, c->side) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
+    const size_t vbytes = (size_t)c->n_act * c->m_pad * 4;
+    const size_t xbytes = std::max((size_t)c->n_act * c->mb_pad * 2, vbytes);
+    for (int b = 0; b < 2; ++b) {
+        if (cudaEventCreateWithFlags(&c->ev_v_ready[b], cudaEventDisableTiming) != cudaSuccess) return LETKF_ECUDA;
+        if (cudaEventCreateWithFlags(&c->ev_v_used[b], cudaEventDisableTiming) != cudaSuccess) return LETKF_ECUDA;
+        if (cudaMalloc(&c->Vbuf[b], vbytes) != cudaSuccess) return LETKF_ENOMEM;
+        c->device_bytes += vbytes;
+    }
+    if (cudaMalloc(&c->Xi_side, xbytes) != cudaSuccess) return LETKF_ENOMEM;
+    c->device_bytes += xbytes;
+    return LETKF_OK;
+}
+
+// The process-noise block of `frame` in buffer frame & 1, drawn on the side stream (after the
+// kernel that last read that buffer) unless it is there already; the main stream waits for it.
+int fused_noise_ready(letkf_ctx* c, unsigned long long frame, const float** v) {
+    const int b = (int)(frame & 1);
+    if (c->v_frame[b] != frame) {
+        if (cudaStreamWaitEvent(c->side, c->ev_v_used[b], 0) != cudaSuccess) return LETKF_ECUDA;
+        const int rc = draw_perturbations_on(c, frame, c->Xi_side, c->Vbuf[b], c->side, c->cublas_side);
+        if (rc) return rc;
+        if (cudaEventRecord(c->ev_v_ready[b], c->side) != cudaSuccess) return LETKF_ECUDA;
+        c->v_frame[b] = frame;
+    }
+    if (cudaStreamWaitEvent(c->stream, c->ev_v_ready[b], 0) != cudaSuccess) return LETKF_ECUDA;
+    *v = static_cast<const float*>(c->Vbuf[b]);
+    return LETKF_OK;
+}
+
+// After the kernel of `frame` is queued: mark its buffer in use and draw frame + 1 into the other.
+int fused_noise_prefetch(letkf_ctx* c, unsigned long long frame) {
+    const int b = (int)(frame & 1), nb = b ^ 1;
+    if (cudaEventRecord(c->ev_v_used[b], c->stream) != cudaSuccess) return LETKF_ECUDA;
+    if (c->v_frame[nb] == frame + 1) return LETKF_OK;
+    if (cudaStreamWaitEvent(c->side, c->ev_v_used[nb], 0) != cudaSuccess) return LETKF_ECUDA;
+    const int rc = draw_perturbations_on(c, frame + 1, c->Xi_side, c->Vbuf[nb], c->side, c->cublas_side);
+    if (rc) return rc;
+    if (cudaEventRecord(c->ev_v_ready[nb], c->side) != cudaSuccess) return LETKF_ECUDA;
+    c->v_frame[nb] = frame + 1;
     return LETKF_OK;
 }
 
 int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast) {
     if (sigma > 0) c->sigma = sigma;
-    int rc = launch_precheck(c, y);    // also resets the work queue
-    if (rc) return rc;
+    int rc;
     FusedArgs A;
     A.X = static_cast<const float*>(c->X[c->cur]);
     A.Xo = static_cast<float*>(c->X[c->cur ^ 1]);
     A.y = static_cast<const float*>(y);
     A.V = nullptr;
     A.vmode = 2;
+    const bool dense_noise = with_forecast && c->Lq;
     if (with_forecast) {
-        if (c->Lq) {
-            if ((rc = draw_perturbations(c, c->frame))) return rc;
-            A.V = static_cast<const float*>(c->V);
+        if (dense_noise) {
+            if ((rc = fused_noise_ready(c, c->frame, &A.V))) return rc;
             A.vmode = 0;
         } else if (c->q_white > 0) {
             A.vmode = 1;
@@ -813,6 +877,7 @@ int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_
     const FusedLayout L = fused_layout(c);
     A.NP = L.NP;
     A.KP = L.KP;
+    A.p = c->p;
     A.inv_sigma = (float)(1.0 / c->sigma);
     A.a = (float)c->a;
     A.q_white = (float)c->q_white;
@@ -833,7 +898,9 @@ int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_
     prof_begin(c, STAGE_FUSED);
     fused_kernel<<<c->fused_grid, FT, c->fused_smem, c->stream>>>(A);
     prof_end(c);
-    return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
+    if (dense_noise) return fused_noise_prefetch(c, c->frame);
+    return LETKF_OK;
 }
 
 }  // namespace letkf

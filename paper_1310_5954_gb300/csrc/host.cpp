@@ -301,6 +301,14 @@ void free_all(letkf_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->cublas) cublasDestroy(c->cublas);
+    if (c->cublas_side) cublasDestroy(c->cublas_side);
+    for (int b = 0; b < 2; ++b) {
+        if (c->Vbuf[b]) cudaFree(c->Vbuf[b]);
+        if (c->ev_v_ready[b]) cudaEventDestroy(c->ev_v_ready[b]);
+        if (c->ev_v_used[b]) cudaEventDestroy(c->ev_v_used[b]);
+    }
+    if (c->Xi_side) cudaFree(c->Xi_side);
+    if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
 }
@@ -425,6 +433,7 @@ int letkf_destroy(letkf_ctx* c) {
     if (!c) return LETKF_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     free_all(c);
     delete c;
     return LETKF_OK;
@@ -526,6 +535,7 @@ int letkf_sync(letkf_ctx* c) {
     if (!c) return LETKF_EINVAL;
     CU(cudaSetDevice(c->device));
     CU(cudaStreamSynchronize(c->stream));
+    if (c->side) CU(cudaStreamSynchronize(c->side));
     int st = 0;
     CU(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) CU(cudaMemset(c->d_status, 0, sizeof(int)));

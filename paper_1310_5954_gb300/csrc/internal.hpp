@@ -90,6 +90,15 @@ struct letkf_ctx {
     size_t device_bytes = 0;
     int fused_smem = 0;             // dynamic shared memory of the fused kernel
     int fused_grid = 0;
+    // fused path: process noise of the next frame drawn on a side stream while the current
+    // frame's kernel runs (double-buffered; v_frame[b] = frame whose draw buffer b holds)
+    cudaStream_t side = nullptr;
+    cublasHandle_t cublas_side = nullptr;
+    cudaEvent_t ev_v_ready[2] = {nullptr, nullptr};
+    cudaEvent_t ev_v_used[2] = {nullptr, nullptr};
+    void* Vbuf[2] = {nullptr, nullptr};
+    void* Xi_side = nullptr;
+    unsigned long long v_frame[2] = {~0ull, ~0ull};
     // stage timing
     int prof_on = 0;
     std::vector<int> prof_stage;            // stage of each record
@@ -116,6 +125,9 @@ size_t plain_smem_bytes(const letkf_ctx* c, int which);
 int launch_precheck(letkf_ctx* c, const void* y);
 int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis);
 int draw_perturbations(letkf_ctx* c, unsigned long long frame);
+// Normals of `frame` into xi, then V = L xi into v_out, on `stream` with `handle`.
+int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream,
+                          cublasHandle_t handle);
 int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host);
 int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
 

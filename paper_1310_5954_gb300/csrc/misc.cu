@@ -180,20 +180,29 @@ int draw_perturbations(letkf_ctx* c, unsigned long long frame) {
 }
 
 int draw_perturbations_impl(letkf_ctx* c, unsigned long long frame) {
+    return draw_perturbations_on(c, frame, c->Xi, c->V, c->stream, c->cublas);
+}
+
+int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream,
+                          cublasHandle_t handle) {
     const int gt = gemm_type_of(c);
     const int nq = (c->n_act + 3) / 4;
     const int g = grid_for((size_t)nq * c->m, 256);
     if (gt == 0)
-        normals_kernel<double><<<g, 256, 0, c->stream>>>((double*)c->Xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
-                                                         (uint32_t)frame);
+        normals_kernel<double><<<g, 256, 0, stream>>>((double*)xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
+                                                      (uint32_t)frame);
     else if (gt == 1)
-        normals_kernel<float><<<g, 256, 0, c->stream>>>((float*)c->Xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
-                                                        (uint32_t)frame);
+        normals_kernel<float><<<g, 256, 0, stream>>>((float*)xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
+                                                     (uint32_t)frame);
     else
-        normals_kernel<__nv_bfloat16><<<g, 256, 0, c->stream>>>((__nv_bfloat16*)c->Xi, c->mb_pad, c->n_act, c->m,
-                                                                c->seed, 1u, (uint32_t)frame);
+        normals_kernel<__nv_bfloat16><<<g, 256, 0, stream>>>((__nv_bfloat16*)xi, c->mb_pad, c->n_act, c->m,
+                                                             c->seed, 1u, (uint32_t)frame);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
-    return noise_gemm(c, c->Lq, c->Xi, gt == 2 ? c->mb_pad : c->m_pad, gt, c->V);
+    cublasHandle_t saved = c->cublas;
+    c->cublas = handle;
+    const int rc = noise_gemm(c, c->Lq, xi, gt == 2 ? c->mb_pad : c->m_pad, gt, v_out);
+    c->cublas = saved;
+    return rc;
 }
 
 int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis) {
