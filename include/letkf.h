@@ -57,7 +57,8 @@ typedef enum letkf_status {
     LETKF_ENONFINITE = -5,  /* non-finite slopes: that frame was rejected, state unchanged */
     LETKF_ESTATE = -6,      /* call out of order (e.g. analyze twice without a forecast) */
     LETKF_ENOCONV = -7,     /* a domain eigensolve hit its sweep limit (result still written) */
-    LETKF_ESCRATCH = -8     /* the problem does not fit letkf_analyze_static's fixed scratch */
+    LETKF_ESCRATCH = -8,    /* the problem does not fit letkf_analyze_static's fixed scratch */
+    LETKF_EBUSY = -9        /* refused for now (letkf_serve.h): HBM budget or frame queue full */
 } letkf_status;
 
 typedef enum letkf_precision {
@@ -105,7 +106,6 @@ typedef struct letkf_info {
     int n_domains;
     int n_loc_max;                  /* largest number of state rows a domain updates */
     int p_loc_max;                  /* largest number of slopes a domain observes */
-    int rank_max;                   /* largest rank of a domain's observation operator */
     int state_bytes;                /* 8 (FP64) or 4 */
     int precision, path;
     unsigned long long frame;       /* frames forecast so far */
@@ -125,6 +125,15 @@ typedef struct letkf_info {
  * in the forecast phase at frame 0.  *out is set to NULL on failure.
  */
 int letkf_create(const letkf_params* params, letkf_ctx** out);
+
+/*
+ * letkf_footprint: device bytes a context created with these parameters holds (geometry
+ * tables, the two ensemble buffers, process-noise buffers and the path's scratch; equal to
+ * letkf_info.device_bytes after letkf_create), computed on the host without touching a GPU.
+ * Creation itself briefly needs up to 2 * n_act^2 * 8 more bytes for the FP64 factors.
+ * LETKF_EINVAL for parameters letkf_create would reject on the host.
+ */
+int letkf_footprint(const letkf_params* params, unsigned long long* bytes);
 
 /* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
 int letkf_destroy(letkf_ctx* ctx);

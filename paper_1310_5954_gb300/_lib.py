@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libletkf.so")
 
 LETKF_OK, LETKF_EINVAL, LETKF_ENOMEM, LETKF_ECUDA = 0, -1, -2, -3
 LETKF_ETIMEOUT, LETKF_ENONFINITE, LETKF_ESTATE, LETKF_ENOCONV = -4, -5, -6, -7
-LETKF_ESCRATCH = -8
+LETKF_ESCRATCH, LETKF_EBUSY = -8, -9
 LETKF_PREC_FP64, LETKF_PREC_FP32, LETKF_PREC_MIXED = 0, 1, 2
 LETKF_PATH_PLAIN, LETKF_PATH_FUSED = 0, 1
 
@@ -47,11 +47,29 @@ class letkf_info(ctypes.Structure):
     _fields_ = [
         ("n_sub", ctypes.c_int), ("n_act", ctypes.c_int), ("n_subv", ctypes.c_int), ("n", ctypes.c_int),
         ("p", ctypes.c_int), ("m", ctypes.c_int), ("n_domains", ctypes.c_int), ("n_loc_max", ctypes.c_int),
-        ("p_loc_max", ctypes.c_int), ("rank_max", ctypes.c_int), ("state_bytes", ctypes.c_int),
+        ("p_loc_max", ctypes.c_int), ("state_bytes", ctypes.c_int),
         ("precision", ctypes.c_int), ("path", ctypes.c_int), ("frame", ctypes.c_ulonglong),
         ("device_bytes", ctypes.c_size_t), ("n_domains_observing", ctypes.c_int),
         ("sum_p_loc", ctypes.c_longlong), ("sum_n_loc", ctypes.c_longlong),
     ]
+
+
+class letkf_server_params(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget", ctypes.c_ulonglong), ("max_systems", ctypes.c_int),
+                ("slots", ctypes.c_int), ("max_pending", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class letkf_frame_record(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_int), ("status", ctypes.c_int), ("frame", ctypes.c_ulonglong),
+                ("t_arrival_ns", ctypes.c_longlong), ("t_launch_ns", ctypes.c_longlong),
+                ("t_done_ns", ctypes.c_longlong), ("batch_systems", ctypes.c_int), ("slot", ctypes.c_int)]
+
+
+class letkf_server_info(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_ulonglong), ("hbm_used", ctypes.c_ulonglong), ("systems", ctypes.c_int),
+                ("frames_waiting", ctypes.c_int), ("frames_in_flight", ctypes.c_int),
+                ("frames_done", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
+                ("batched_systems", ctypes.c_ulonglong)]
 
 
 N_STAGES = 8
@@ -79,6 +97,22 @@ _SIGS = {
     "letkf_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
     "letkf_umma_selftest": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            _VP]),
+    "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
+    # letkf_serve.h
+    "letkf_now_ns": (ctypes.c_longlong, []),
+    "letkf_server_create": (ctypes.c_int, [ctypes.POINTER(letkf_server_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "letkf_server_destroy": (ctypes.c_int, [_VP]),
+    "letkf_server_admit": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_int)]),
+    "letkf_server_release": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "letkf_server_set_output": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
+    "letkf_server_submit": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_longlong]),
+    "letkf_server_pump": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "letkf_server_drain": (ctypes.c_int, [_VP]),
+    "letkf_server_records": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_frame_record), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "letkf_server_context": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "letkf_server_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_server_info)]),
+    "letkf_server_replay": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -188,8 +222,98 @@ def letkf_umma_selftest(a_ptr: int, b_ptr: int, d_ptr: int, n: int, k: int, term
     return load().letkf_umma_selftest(a_ptr, b_ptr, d_ptr, n, k, terms, b_layout, stream or None)
 
 
+def letkf_footprint(params: letkf_params) -> int:
+    out = ctypes.c_ulonglong()
+    _check(load().letkf_footprint(ctypes.byref(params), ctypes.byref(out)), "letkf_footprint")
+    return out.value
+
+
+# ---- letkf_serve.h ---------------------------------------------------------------------------
+def letkf_now_ns() -> int:
+    return load().letkf_now_ns()
+
+
+def letkf_server_create(params: letkf_server_params) -> int:
+    out = ctypes.c_void_p()
+    _check(load().letkf_server_create(ctypes.byref(params), ctypes.byref(out)), "letkf_server_create")
+    return out.value
+
+
+def letkf_server_destroy(server: int) -> int:
+    return load().letkf_server_destroy(server)
+
+
+def letkf_server_admit(server: int, params: letkf_params) -> int:
+    """System id; raises LETKFError (status LETKF_EBUSY when the HBM budget is full)."""
+    sid = ctypes.c_int(-1)
+    _check(load().letkf_server_admit(server, ctypes.byref(params), ctypes.byref(sid)), "letkf_server_admit")
+    return sid.value
+
+
+def letkf_server_release(server: int, sid: int) -> int:
+    return _check(load().letkf_server_release(server, int(sid)), "letkf_server_release")
+
+
+def letkf_server_set_output(server: int, sid: int, host_ptr: int, n_frames: int) -> int:
+    return _check(load().letkf_server_set_output(server, int(sid), host_ptr or None, int(n_frames)),
+                  "letkf_server_set_output")
+
+
+def letkf_server_submit(server: int, sid: int, y_ptr: int, sigma: float = 0.0, t_arrival_ns: int = 0) -> int:
+    """Returns LETKF_OK or LETKF_EBUSY (queue full); raises on other errors."""
+    rc = load().letkf_server_submit(server, int(sid), y_ptr, float(sigma), int(t_arrival_ns))
+    if rc not in (LETKF_OK, LETKF_EBUSY):
+        raise LETKFError(rc, "letkf_server_submit")
+    return rc
+
+
+def letkf_server_pump(server: int) -> int:
+    n = ctypes.c_int()
+    _check(load().letkf_server_pump(server, ctypes.byref(n)), "letkf_server_pump")
+    return n.value
+
+
+def letkf_server_drain(server: int) -> int:
+    return _check(load().letkf_server_drain(server), "letkf_server_drain")
+
+
+def letkf_server_records(server: int, max_records: int = 4096) -> list:
+    buf = (letkf_frame_record * max_records)()
+    out = []
+    while True:
+        n = ctypes.c_int()
+        _check(load().letkf_server_records(server, buf, max_records, ctypes.byref(n)), "letkf_server_records")
+        out.extend({f: getattr(buf[i], f) for f, _ in letkf_frame_record._fields_} for i in range(n.value))
+        if n.value < max_records:
+            return out
+
+
+def letkf_server_context(server: int, sid: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().letkf_server_context(server, int(sid), ctypes.byref(out)), "letkf_server_context")
+    return out.value
+
+
+def letkf_server_get_info(server: int) -> dict:
+    info = letkf_server_info()
+    _check(load().letkf_server_get_info(server, ctypes.byref(info)), "letkf_server_get_info")
+    return {f: getattr(info, f) for f, _ in letkf_server_info._fields_}
+
+
+def letkf_server_replay(server: int, sys_ids, t_ns, y_ptrs, sigma=None) -> int:
+    """Real-time replay of an arrival trace (arrays of equal length); returns the refused count."""
+    n = len(sys_ids)
+    s = (ctypes.c_int * n)(*[int(v) for v in sys_ids])
+    t = (ctypes.c_longlong * n)(*[int(v) for v in t_ns])
+    y = (ctypes.c_void_p * n)(*[int(v) for v in y_ptrs])
+    sg = None if sigma is None else (ctypes.c_double * n)(*[float(v) for v in sigma])
+    refused = ctypes.c_int()
+    _check(load().letkf_server_replay(server, n, s, t, y, sg, ctypes.byref(refused)), "letkf_server_replay")
+    return refused.value
+
+
 def declared_functions(header: str) -> list:
     """Names of the functions declared in a letkf header (used to check the exports)."""
     import re
     text = open(header).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(letkf_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(letkf_\w+)\s*\(", text, re.M)))

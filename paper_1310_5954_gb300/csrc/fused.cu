@@ -40,20 +40,9 @@ constexpr int MT = 128;                  // MMA rows
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
 constexpr int TM_G = 0, TM_P = 128, TM_Y = 256, TM_Z = 384, TM_COLS = 512;
 
-struct Ctrl {
-    uint64_t bar_load;
-    uint64_t bar_mma;
-    uint32_t tmem_base;
-    int item;
-    int abort;
-    int flag;
-    float s;
-    float rn;
-    float red[FT / 32];
-    double redd[FT / 32];
-};
-
-struct FusedArgs {
+// One system's frame in a batch.  Work items item0 .. item0 + n_dom - 1 of the batch are the
+// system's domains in its own processing order (most expensive first).
+struct SysDesc {
     const float* X;
     float* Xo;
     const float* y;
@@ -61,16 +50,46 @@ struct FusedArgs {
     float* xpred;
     DomainTables tab;
     int* status;
-    int* frame_bad;
-    int* queue;          // [0] next work item, [1] CTAs done (the last one resets both)
-    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, p;
+    int* frame_bad;      // frame-level rejection flag, written at the end of the launch
+    int* dom_bad;        // set by any domain that meets a non-finite slope; reset at the end
+    unsigned long long seed;
+    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, item0;
     float inv_sigma, a, q_white;
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
-    unsigned long long seed;
     uint32_t frame;
-    // shared-memory layout (bytes from the dynamic base)
+    // shared-memory layout (bytes from the dynamic base); vec and XE start at the same offset
+    // for every system, so a region below off_big never overlaps another system's operands
     int off_vec, off_xe, off_xh, off_big, sz_op, sz_opg, sz_a;
+};
+
+struct Ctrl {
+    uint64_t bar_load;
+    uint64_t bar_mma;
+    uint32_t tmem_base;
+    int item;            // global work item (over all systems of the batch)
+    int sys;             // its system
+    int dom;             // its domain
+    int loaded;          // its bulk loads are issued
+    int last;            // this CTA finished last
+    int abort;
+    int flag;
+    float s;
+    float rn;
+    float red[FT / 32];
+    double redd[FT / 32];
+    SysDesc sd;          // the current item's system (copied from the kernel parameters)
+};
+static_assert(sizeof(Ctrl) <= 1024, "control block overlaps the vector area");
+
+// Kernel parameters of one launch (read through the constant bank).  One launch of one
+// system and one launch of many run the same code, so a system's results do not depend on
+// what shares its launch.
+struct FusedBatch {
+    SysDesc sys[FUSED_MAX_BATCH];
+    int n_sys;
+    int n_items;
+    int* queue;          // [0] next work item, [1] CTAs done (the last one resets both)
 };
 
 // Write 8 consecutive K-values of row `row` into the hi (and optionally lo) operand: hi is the
@@ -143,9 +162,8 @@ __device__ __forceinline__ float block_sum(Ctrl* ctl, float v) {
     return s;
 }
 
-// Domains that take no analysis (rejected frame, or no observation): rows copied exactly, and
-// the forecast applied unless the frame was rejected.
-__device__ void simt_rows(const FusedArgs& A, int e0, int n_own, bool rejected) {
+// Domains with no observation: rows copied exactly, and the forecast applied.
+__device__ __forceinline__ void simt_rows(const SysDesc& A, int e0, int n_own) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = warp; e < n_own; e += FT / 32) {
         const int j = A.tab.own[e0 + e];
@@ -157,7 +175,7 @@ __device__ void simt_rows(const FusedArgs& A, int e0, int n_own, bool rejected) 
         for (int i = lane; i < A.m; i += 32) {
             const float a1 = x1[i];
             float n1 = a1;
-            if (rejected || !A.with_forecast) {
+            if (!A.with_forecast) {
                 o1[i] = a1;
                 o2[i] = x2[i];
             } else {
@@ -180,16 +198,10 @@ __device__ void simt_rows(const FusedArgs& A, int e0, int n_own, bool rejected) 
     }
 }
 
-// Does domain `item` go through the tensor-core analysis (as opposed to the row copy)?
-__device__ __forceinline__ bool analysed(const FusedArgs& A, int item, bool rejected) {
-    if (item >= A.n_dom || rejected) return false;
-    const int d = A.tab.order[item];
-    return A.tab.obs_off[d + 1] > A.tab.obs_off[d];
-}
-
-// Thread 0: bulk copies of the domain's halo rows (observed instant) and own rows.
-__device__ void issue_loads(const FusedArgs& A, int item, float* Xh, float* XE, uint64_t* bar) {
-    const int d = A.tab.order[item];
+// Thread 0: bulk copies of domain d's halo rows (observed instant) and own rows.
+__device__ __forceinline__ void issue_loads(const SysDesc& A, int d, unsigned char* smem, uint64_t* bar) {
+    float* Xh = reinterpret_cast<float*>(smem + A.off_xh);
+    float* XE = reinterpret_cast<float*>(smem + A.off_xe);
     const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
     const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
     const int n_e = A.with_forecast ? n_own : 2 * n_own;
@@ -203,45 +215,65 @@ __device__ void issue_loads(const FusedArgs& A, int item, float* Xh, float* XE, 
     }
 }
 
-__global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
+// Thread 0: take the next work item of the batch.  Its loads are issued at once when they
+// cannot overwrite shared memory still in use (everything at or above busy_from).
+__device__ void fetch_item(const FusedBatch& B, Ctrl* ctl, unsigned char* smem, int busy_from) {
+    const int g = atomicAdd(B.queue, 1);
+    ctl->item = g;
+    ctl->loaded = 0;
+    if (g >= B.n_items) return;
+    int s = 0;
+    while (s + 1 < B.n_sys && g >= B.sys[s + 1].item0) ++s;
+    const SysDesc& A = B.sys[s];
+    const int d = A.tab.order[g - A.item0];
+    ctl->sys = s;
+    ctl->dom = d;
+    if (A.tab.obs_off[d + 1] > A.tab.obs_off[d] && A.off_big <= busy_from) {
+        issue_loads(A, d, smem, &ctl->bar_load);
+        ctl->loaded = 1;
+    }
+}
+
+// The last CTA of the launch: systems whose frame met a non-finite slope get their state back
+// unchanged (and the prediction of that state); every system's frame flag is published and the
+// per-launch counters are reset for the next launch.
+__device__ void finish_batch(const FusedBatch& B) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int si = 0; si < B.n_sys; ++si) {
+        const SysDesc& A = B.sys[si];
+        const int bad = *reinterpret_cast<volatile int*>(A.dom_bad);
+        if (bad) {
+            const size_t n4 = (size_t)2 * A.n_act * A.m_pad / 4;
+            const float4* src = reinterpret_cast<const float4*>(A.X);
+            float4* dst = reinterpret_cast<float4*>(A.Xo);
+            for (size_t t = tid; t < n4; t += FT) dst[t] = src[t];
+            if (A.xpred)
+                for (int j = warp; j < A.n_act; j += FT / 32) {
+                    float sm_ = 0.f;
+                    for (int i = lane; i < A.m; i += 32) sm_ += A.X[(size_t)j * A.m_pad + i];
+                    sm_ = warp_sum(sm_);
+                    if (lane == 0) A.xpred[j] = sm_ / (float)A.m;
+                }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            *A.frame_bad = bad;
+            *A.dom_bad = 0;
+        }
+    }
+    if (tid == 0) {
+        B.queue[0] = 0;
+        B.queue[1] = 0;
+        __threadfence();
+    }
+}
+
+__global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ FusedBatch B) {
     extern __shared__ __align__(1024) unsigned char smem[];
     Ctrl* ctl = reinterpret_cast<Ctrl*>(smem);
-    float* vec = reinterpret_cast<float*>(smem + A.off_vec);
-    float* xh_mean = vec;            // 256 (halo actuators)
-    float* xe_mean = vec + 256;      // 128 (own rows)
-    float* bvec = vec + 384;         // 128
-    float* wbar = vec + 512;         // 128
-    float* vtmp = vec + 640;         // 2 x 128 (column-half partial sums)
-    float* vv = vec + 896;           // 128
-    float* vr = vec + 1024;          // 128
-    float* uvec = vec + 1152;        // 128 (mean update of each own row)
-    float* dtv = vec + 1280;         // 128 (innovation d / sigma of each observed slope)
-    float* tvv = vec + 1408;         // 128 (slope-space residual)
-    float* XE = reinterpret_cast<float*>(smem + A.off_xe);
-    float* Xh = reinterpret_cast<float*>(smem + A.off_xh);   // halo anomalies, kept for the refinement
-    // Operand buffers hold only the rows that can be non-zero (NP, or RA for the transform's A);
-    // a 128-row MMA reads the rows beyond them from whatever follows, which only feeds output
-    // rows that are never used.
-    unsigned char* big = smem + A.off_big;
-    unsigned char* opg_h = big;
-    unsigned char* opg_l = big + A.sz_opg;
-    unsigned char* Yh = big;
-    unsigned char* Yl = big + A.sz_op;
-    unsigned char* Zh = big + 2 * A.sz_op;
-    unsigned char* Zl = big + 3 * A.sz_op;
-    unsigned char* Th = big + 4 * A.sz_op;
-    unsigned char* Tl = big + 5 * A.sz_op;
-    unsigned char* Ah = big;                 // transform operands reuse the NS region
-    unsigned char* Al = big + A.sz_a;
-    unsigned char* Bh = big + 2 * A.sz_a;
-    unsigned char* Bl = big + 2 * A.sz_a + A.sz_op;
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = 32 * (warp & 3) + lane;          // TMEM lane / matrix row of this thread
     const int hh = warp >> 2;                        // column half of this thread
-    const int m = A.m, NP = A.NP, KP = A.KP, half = NP / 2, nq = half / 8;
-    const int col0 = hh * half;                      // first column of this thread's half-row
-    const float c = (float)(m - 1);
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 
     if (tid == 0) {
@@ -258,49 +290,87 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ctl->tmem_base;
-    const uint32_t tl = tbase + lane_off + (uint32_t)col0;   // this thread's lane, first column
     uint32_t ph_load = 0, ph_mma = 0;
-    // frame ingest: every CTA checks the whole slope vector, so all of them agree on
-    // rejecting a frame with a non-finite slope (the ensemble is then left unchanged)
-    int nonfinite = 0;
-    for (int i = tid; i < A.p; i += FT)
-        if (!isfinite(A.y[i])) nonfinite = 1;
-    const bool rejected = __syncthreads_or(nonfinite) != 0;
-    if (blockIdx.x == 0 && tid == 0) {
-        *A.frame_bad = rejected ? 1 : 0;
-        if (rejected) atomicOr(A.status, ST_NONFINITE);
-    }
 
-    if (tid == 0) {
-        const int it0 = atomicAdd(A.queue, 1);
-        ctl->item = it0;
-        if (analysed(A, it0, rejected)) issue_loads(A, it0, Xh, XE, &ctl->bar_load);
-    }
+    if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
     __syncthreads();
-    int item = ctl->item;
 
-    while (item < A.n_dom && !ctl->abort) {
-        const int d = A.tab.order[item];
+    while (ctl->item < B.n_items && !ctl->abort) {
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&B.sys[ctl->sys]);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&ctl->sd);
+            for (int t = tid; t < (int)(sizeof(SysDesc) / 4); t += FT) dst[t] = src[t];
+            __syncthreads();
+        }
+        const SysDesc A = ctl->sd;   // by value: fields stay in registers across barriers
+        const int d = ctl->dom;
+        float* vec = reinterpret_cast<float*>(smem + A.off_vec);
+        float* xh_mean = vec;            // 256 (halo actuators)
+        float* xe_mean = vec + 256;      // 128 (own rows)
+        float* bvec = vec + 384;         // 128
+        float* wbar = vec + 512;         // 128
+        float* vtmp = vec + 640;         // 2 x 128 (column-half partial sums)
+        float* vv = vec + 896;           // 128
+        float* vr = vec + 1024;          // 128
+        float* uvec = vec + 1152;        // 128 (mean update of each own row)
+        float* dtv = vec + 1280;         // 128 (innovation d / sigma of each observed slope)
+        float* tvv = vec + 1408;         // 128 (slope-space residual)
+        float* XE = reinterpret_cast<float*>(smem + A.off_xe);
+        float* Xh = reinterpret_cast<float*>(smem + A.off_xh);   // halo anomalies, kept for the refinement
+        // Operand buffers hold only the rows that can be non-zero (NP, or RA for the transform's A);
+        // a 128-row MMA reads the rows beyond them from whatever follows, which only feeds output
+        // rows that are never used.
+        unsigned char* big = smem + A.off_big;
+        unsigned char* opg_h = big;
+        unsigned char* opg_l = big + A.sz_opg;
+        unsigned char* Yh = big;
+        unsigned char* Yl = big + A.sz_op;
+        unsigned char* Zh = big + 2 * A.sz_op;
+        unsigned char* Zl = big + 3 * A.sz_op;
+        unsigned char* Th = big + 4 * A.sz_op;
+        unsigned char* Tl = big + 5 * A.sz_op;
+        unsigned char* Ah = big;                 // transform operands reuse the NS region
+        unsigned char* Al = big + A.sz_a;
+        unsigned char* Bh = big + 2 * A.sz_a;
+        unsigned char* Bl = big + 2 * A.sz_a + A.sz_op;
+        const int m = A.m, NP = A.NP, KP = A.KP, half = NP / 2, nq = half / 8;
+        const int col0 = hh * half;                      // first column of this thread's half-row
+        const float c = (float)(m - 1);
+        const uint32_t tl = tbase + lane_off + (uint32_t)col0;   // this thread's lane, first column
+
         const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
         const int o0 = A.tab.obs_off[d], n_obs = A.tab.obs_off[d + 1] - o0;
         const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
         const int p_loc = 2 * n_obs;
         const int n_e = A.with_forecast ? n_own : 2 * n_own;
-        if (rejected || n_obs == 0) {
-            simt_rows(A, e0, n_own, rejected);
+        if (n_obs == 0) {
+            simt_rows(A, e0, n_own);
             __syncthreads();
-            if (tid == 0) {
-                const int nx = atomicAdd(A.queue, 1);
-                ctl->item = nx;
-                if (analysed(A, nx, rejected)) issue_loads(A, nx, Xh, XE, &ctl->bar_load);
-            }
+            if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
             __syncthreads();
-            item = ctl->item;
             continue;
         }
-        // ---- 1. the halo rows of the observed instant and the own rows (issued earlier)
+        if (tid == 0 && !ctl->loaded) issue_loads(A, d, smem, &ctl->bar_load);
+        // ---- frame ingest: a non-finite slope in this domain's observation region rejects the
+        //      system's frame (its state is restored when the launch ends)
+        int nonfinite = 0;
+        for (int t = tid; t < n_obs; t += FT) {
+            const int sub = A.tab.obs_sub[o0 + t];
+            if (!isfinite(A.y[sub]) || !isfinite(A.y[A.n_subv + sub])) nonfinite = 1;
+        }
+        const bool dom_bad = __syncthreads_or(nonfinite) != 0;
+        // ---- 1. the halo rows of the observed instant and the own rows
         if (!wait_all(ctl, &ctl->bar_load, ph_load, A.status)) break;
         ph_load ^= 1;
+        if (dom_bad) {
+            if (tid == 0) {
+                atomicExch(A.dom_bad, 1);
+                atomicOr(A.status, ST_NONFINITE);
+                fetch_item(B, ctl, smem, 1 << 30);
+            }
+            __syncthreads();
+            continue;
+        }
         // ---- 2. halo anomalies; slopes (x and y of each subaperture interleaved along K:
         //        k = 2 s + direction) and the innovation row as the Gram operand
         for (int j = warp; j < n_h; j += FT / 32) {
@@ -594,9 +664,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
             issue_product(tbase + TM_P, Ah, Al, Bh, Bl, NP, NP, A.tr_terms, 1);   // X'_E T
             mma_commit(&ctl->bar_mma);
             // the halo and own-row tiles are free now: fetch the next domain's under this product
-            const int nx = atomicAdd(A.queue, 1);
-            ctl->item = nx;
-            if (analysed(A, nx, rejected)) issue_loads(A, nx, Xh, XE, &ctl->bar_load);
+            fetch_item(B, ctl, smem, A.off_big);
         }
         if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
         ph_mma ^= 1;
@@ -661,23 +729,21 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(FusedArgs A) {
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        item = ctl->item;
     }
     // a wait that ran out may leave bulk copies in flight: give them a bounded time to land
     if (ctl->abort && tid == 0) mbar_wait_bounded(&ctl->bar_load, ph_load, WAIT_CYCLES);
-    // the last CTA to finish resets the work queue for the next launch (all fetches are done)
-    if (tid == 0) {
-        __threadfence();
-        if (atomicAdd(&A.queue[1], 1) == (int)gridDim.x - 1) {
-            A.queue[0] = 0;
-            A.queue[1] = 0;
-            __threadfence();
-        }
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tbase, TM_COLS);
+    // the last CTA to finish (all work items taken and done) closes the launch
+    if (tid == 0) {
+        __threadfence();
+        ctl->last = atomicAdd(&B.queue[1], 1) == (int)gridDim.x - 1;
+        if (ctl->last) __threadfence();
+    }
+    __syncthreads();
+    if (ctl->last) finish_batch(B);
 }
 
 // Self-test of the tensor-core product: D (128 x N) = A (128 x K) * B (N x K)^T, operands
@@ -792,7 +858,8 @@ int fused_prepare(letkf_ctx* c) {
     if (L.total > 227 * 1024) return LETKF_EINVAL;
     if (h.n_h_max > 255 || h.n_loc_max > MT) return LETKF_EINVAL;
     c->fused_smem = L.total;
-    if (cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
+    static_assert(sizeof(FusedBatch) < 32000, "kernel parameters too large");
+    if (cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
         return LETKF_ECUDA;
     // One CTA per SM pulling domains from the work queue: domains differ in cost (edge domains
     // see fewer subapertures), so the full grid balances better than fewer, evenly loaded CTAs.
@@ -816,9 +883,11 @@ int fused_prepare(letkf_ctx* c) {
     return LETKF_OK;
 }
 
+namespace {
+
 // The process-noise block of `frame` in buffer frame & 1, drawn on the side stream (after the
-// kernel that last read that buffer) unless it is there already; the main stream waits for it.
-int fused_noise_ready(letkf_ctx* c, unsigned long long frame, const float** v) {
+// kernel that last read that buffer) unless it is there already; `stream` waits for it.
+int noise_ready(letkf_ctx* c, unsigned long long frame, cudaStream_t stream, const float** v) {
     const int b = (int)(frame & 1);
     if (c->v_frame[b] != frame) {
         if (cudaStreamWaitEvent(c->side, c->ev_v_used[b], 0) != cudaSuccess) return LETKF_ECUDA;
@@ -827,15 +896,16 @@ int fused_noise_ready(letkf_ctx* c, unsigned long long frame, const float** v) {
         if (cudaEventRecord(c->ev_v_ready[b], c->side) != cudaSuccess) return LETKF_ECUDA;
         c->v_frame[b] = frame;
     }
-    if (cudaStreamWaitEvent(c->stream, c->ev_v_ready[b], 0) != cudaSuccess) return LETKF_ECUDA;
+    if (cudaStreamWaitEvent(stream, c->ev_v_ready[b], 0) != cudaSuccess) return LETKF_ECUDA;
     *v = static_cast<const float*>(c->Vbuf[b]);
     return LETKF_OK;
 }
 
-// After the kernel of `frame` is queued: mark its buffer in use and draw frame + 1 into the other.
-int fused_noise_prefetch(letkf_ctx* c, unsigned long long frame) {
+// After the kernel of `frame` is queued on `stream`: mark its buffer in use and draw frame + 1
+// into the other one.
+int noise_prefetch(letkf_ctx* c, unsigned long long frame, cudaStream_t stream) {
     const int b = (int)(frame & 1), nb = b ^ 1;
-    if (cudaEventRecord(c->ev_v_used[b], c->stream) != cudaSuccess) return LETKF_ECUDA;
+    if (cudaEventRecord(c->ev_v_used[b], stream) != cudaSuccess) return LETKF_ECUDA;
     if (c->v_frame[nb] == frame + 1) return LETKF_OK;
     if (cudaStreamWaitEvent(c->side, c->ev_v_used[nb], 0) != cudaSuccess) return LETKF_ECUDA;
     const int rc = draw_perturbations_on(c, frame + 1, c->Xi_side, c->Vbuf[nb], c->side, c->cublas_side);
@@ -845,62 +915,106 @@ int fused_noise_prefetch(letkf_ctx* c, unsigned long long frame) {
     return LETKF_OK;
 }
 
-int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast) {
-    if (sigma > 0) c->sigma = sigma;
-    int rc;
-    FusedArgs A;
-    A.X = static_cast<const float*>(c->X[c->cur]);
-    A.Xo = static_cast<float*>(c->X[c->cur ^ 1]);
-    A.y = static_cast<const float*>(y);
-    A.V = nullptr;
-    A.vmode = 2;
-    const bool dense_noise = with_forecast && c->Lq;
-    if (with_forecast) {
-        if (dense_noise) {
-            if ((rc = fused_noise_ready(c, c->frame, &A.V))) return rc;
-            A.vmode = 0;
+// Descriptor of system c's next frame; `stream` is the stream the kernel will run on.
+int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
+    letkf_ctx* c = f.c;
+    if (f.sigma > 0) c->sigma = f.sigma;
+    S->X = static_cast<const float*>(c->X[c->cur]);
+    S->Xo = static_cast<float*>(c->X[c->cur ^ 1]);
+    S->y = static_cast<const float*>(f.y);
+    S->V = nullptr;
+    S->vmode = 2;
+    if (f.with_forecast) {
+        if (c->Lq) {
+            const int rc = noise_ready(c, c->frame, stream, &S->V);
+            if (rc) return rc;
+            S->vmode = 0;
         } else if (c->q_white > 0) {
-            A.vmode = 1;
+            S->vmode = 1;
         }
     }
-    A.xpred = static_cast<float*>(xpred);
-    A.tab = c->tab;
-    A.status = c->d_status;
-    A.frame_bad = c->d_frame_bad;
-    A.queue = c->d_queue;
-    A.m = c->m;
-    A.m_pad = c->m_pad;
-    A.n_act = c->n_act;
-    A.n_subv = c->n_subv;
-    A.n_dom = c->n_dom;
-    A.row_obs = c->obs_block == 1 ? c->n_act : 0;
+    S->xpred = static_cast<float*>(f.xpred);
+    S->tab = c->tab;
+    S->status = c->d_status;
+    S->frame_bad = c->d_frame_bad;
+    S->dom_bad = c->d_queue + 2;
+    S->seed = c->seed;
+    S->m = c->m;
+    S->m_pad = c->m_pad;
+    S->n_act = c->n_act;
+    S->n_subv = c->n_subv;
+    S->n_dom = c->n_dom;
+    S->row_obs = c->obs_block == 1 ? c->n_act : 0;
     const FusedLayout L = fused_layout(c);
-    A.NP = L.NP;
-    A.KP = L.KP;
-    A.p = c->p;
-    A.inv_sigma = (float)(1.0 / c->sigma);
-    A.a = (float)c->a;
-    A.q_white = (float)c->q_white;
-    A.with_forecast = with_forecast;
-    A.gram_terms = c->precision == LETKF_PREC_MIXED ? 1 : 3;
-    A.tr_terms = 3;   // single-BF16 anomalies in the transform move the residual variance by ~2 %
-    A.max_it = 40;
-    A.s_split = 8.0f;
-    A.seed = c->seed;
-    A.frame = (uint32_t)c->frame;
-    A.off_vec = L.off_vec;
-    A.off_xe = L.off_xe;
-    A.off_xh = L.off_xh;
-    A.off_big = L.off_big;
-    A.sz_op = L.sz_op;
-    A.sz_opg = L.sz_opg;
-    A.sz_a = L.sz_a;
-    prof_begin(c, STAGE_FUSED);
-    fused_kernel<<<c->fused_grid, FT, c->fused_smem, c->stream>>>(A);
-    prof_end(c);
-    if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
-    if (dense_noise) return fused_noise_prefetch(c, c->frame);
+    S->NP = L.NP;
+    S->KP = L.KP;
+    S->inv_sigma = (float)(1.0 / c->sigma);
+    S->a = (float)c->a;
+    S->q_white = (float)c->q_white;
+    S->with_forecast = f.with_forecast;
+    S->gram_terms = c->precision == LETKF_PREC_MIXED ? 1 : 3;
+    S->tr_terms = 3;   // single-BF16 anomalies in the transform move the residual variance by ~2 %
+    S->max_it = 40;
+    S->s_split = 8.0f;
+    S->frame = (uint32_t)c->frame;
+    S->off_vec = L.off_vec;
+    S->off_xe = L.off_xe;
+    S->off_xh = L.off_xh;
+    S->off_big = L.off_big;
+    S->sz_op = L.sz_op;
+    S->sz_opg = L.sz_opg;
+    S->sz_a = L.sz_a;
     return LETKF_OK;
+}
+
+int launch_batch(const FusedFrame* f, const int* order, int n, int* queue, cudaStream_t stream, int sms) {
+    thread_local FusedBatch B;   // host staging of the kernel parameters
+    int items = 0, smem = 0;
+    for (int k = 0; k < n; ++k) {
+        SysDesc& S = B.sys[k];
+        const int rc = make_desc(f[order[k]], stream, &S);
+        if (rc) return rc;
+        S.item0 = items;
+        items += S.n_dom;
+        smem = std::max(smem, f[order[k]].c->fused_smem);
+    }
+    B.n_sys = n;
+    B.n_items = items;
+    B.queue = queue;
+    fused_kernel<<<std::min(sms, items), FT, smem, stream>>>(B);
+    if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
+    for (int k = 0; k < n; ++k) {
+        letkf_ctx* c = f[order[k]].c;
+        if (f[order[k]].with_forecast && c->Lq) {
+            const int rc = noise_prefetch(c, c->frame, stream);
+            if (rc) return rc;
+        }
+    }
+    return LETKF_OK;
+}
+
+}  // namespace
+
+int fused_batch(const FusedFrame* f, int n, int* queue, cudaStream_t stream) {
+    if (n < 1 || n > FUSED_MAX_BATCH) return LETKF_EINVAL;
+    // most expensive domains first: systems by ensemble size, then by their largest domain
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+        const letkf_ctx* a = f[u].c;
+        const letkf_ctx* b = f[v].c;
+        if (a->m != b->m) return a->m > b->m;
+        return a->host.p_loc_max > b->host.p_loc_max;
+    });
+    return launch_batch(f, order.data(), n, queue, stream, f[0].c->sms);
+}
+
+int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast) {
+    FusedFrame f{c, y, sigma, xpred, with_forecast};
+    prof_begin(c, STAGE_FUSED);
+    const int rc = fused_batch(&f, 1, c->d_queue, c->stream);
+    prof_end(c);
+    return rc;
 }
 
 }  // namespace letkf

@@ -12,7 +12,6 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
-#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -53,77 +52,7 @@ std::vector<uint8_t> pupil_mask(int n, double obstruction) {
     return mask;
 }
 
-// Orthonormal basis Q (p x r, column-major) of the column space of A (p x n,
-// column-major) by Householder QR with column pivoting, rank by a relative
-// pivot threshold.  Returns r.
-int range_basis(const std::vector<double>& A_in, int p, int n, std::vector<double>& Q) {
-    std::vector<double> A = A_in;
-    std::vector<int> perm(n);
-    std::iota(perm.begin(), perm.end(), 0);
-    std::vector<double> norms(n);
-    double max0 = 0.0;
-    for (int j = 0; j < n; ++j) {
-        double s = 0;
-        for (int i = 0; i < p; ++i) s += A[(size_t)j * p + i] * A[(size_t)j * p + i];
-        norms[j] = s;
-        max0 = std::max(max0, s);
-    }
-    const int kmax = std::min(p, n);
-    std::vector<std::vector<double>> hv;  // Householder vectors (length p, zeros above k)
-    std::vector<double> beta;
-    int r = 0;
-    for (int k = 0; k < kmax; ++k) {
-        // recompute remaining norms on rows k..p-1 (robust, sizes are small)
-        int piv = -1;
-        double best = -1.0;
-        for (int j = k; j < n; ++j) {
-            double s = 0;
-            for (int i = k; i < p; ++i) s += A[(size_t)j * p + i] * A[(size_t)j * p + i];
-            if (s > best) { best = s; piv = j; }
-        }
-        if (best <= 1e-20 * std::max(max0, 1e-300)) break;
-        if (piv != k) {
-            for (int i = 0; i < p; ++i) std::swap(A[(size_t)k * p + i], A[(size_t)piv * p + i]);
-            std::swap(perm[k], perm[piv]);
-        }
-        std::vector<double> v(p, 0.0);
-        double alpha = 0;
-        for (int i = k; i < p; ++i) alpha += A[(size_t)k * p + i] * A[(size_t)k * p + i];
-        alpha = std::sqrt(alpha);
-        const double x0 = A[(size_t)k * p + k];
-        if (x0 > 0) alpha = -alpha;
-        for (int i = k; i < p; ++i) v[i] = A[(size_t)k * p + i];
-        v[k] -= alpha;
-        double vv = 0;
-        for (int i = k; i < p; ++i) vv += v[i] * v[i];
-        const double bt = vv > 0 ? 2.0 / vv : 0.0;
-        for (int j = k; j < n; ++j) {
-            double s = 0;
-            for (int i = k; i < p; ++i) s += v[i] * A[(size_t)j * p + i];
-            s *= bt;
-            for (int i = k; i < p; ++i) A[(size_t)j * p + i] -= s * v[i];
-        }
-        hv.push_back(v);
-        beta.push_back(bt);
-        r = k + 1;
-    }
-    // Q = H_0 H_1 ... H_{r-1} [I_r; 0]
-    Q.assign((size_t)p * r, 0.0);
-    for (int j = 0; j < r; ++j) Q[(size_t)j * p + j] = 1.0;
-    for (int k = r - 1; k >= 0; --k) {
-        const std::vector<double>& v = hv[k];
-        for (int j = 0; j < r; ++j) {
-            double s = 0;
-            for (int i = k; i < p; ++i) s += v[i] * Q[(size_t)j * p + i];
-            s *= beta[k];
-            for (int i = k; i < p; ++i) Q[(size_t)j * p + i] -= s * v[i];
-        }
-    }
-    return r;
-}
-
-void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obstruction, int b, int halo,
-                 bool factors) {
+void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obstruction, int b, int halo) {
     h.n_sub = n;
     if (sub_valid) {
         h.sub_valid.assign(sub_valid, sub_valid + (size_t)n * n);
@@ -167,9 +96,7 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
     h.obs_off = {0};
     h.halo_off = {0};
     h.own.clear(); h.obs_sub.clear(); h.obs_corner.clear(); h.halo.clear();
-    h.rank.clear(); h.fac_off.clear(); h.fac.clear();
-    h.n_loc_max = h.p_loc_max = h.n_h_max = h.rank_max = 0;
-    std::map<std::vector<int>, std::pair<int, int>> cache;  // local pattern -> (rank, fac_off)
+    h.n_loc_max = h.p_loc_max = h.n_h_max = 0;
     std::vector<double> cost;
     for (int I = 0; I < nb; ++I) {
         for (int J = 0; J < nb; ++J) {
@@ -226,45 +153,6 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
             h.n_loc_max = std::max(h.n_loc_max, n_loc);
             h.p_loc_max = std::max(h.p_loc_max, p_loc);
             h.n_h_max = std::max(h.n_h_max, n_h);
-            int rk = 0, off = 0;
-            if (factors && p_loc > 0) {
-                // pattern key: sizes plus the packed corner list (local structure of D_loc)
-                std::vector<int> key = {n_h, p_loc};
-                key.insert(key.end(), corners.begin(), corners.end());
-                auto it = cache.find(key);
-                if (it != cache.end()) {
-                    rk = it->second.first;
-                    off = it->second.second;
-                } else {
-                    // D_loc (p_loc x n_h) column-major: x-slopes then y-slopes (Fried, Sect. 3)
-                    const int ns = (int)subs.size();
-                    std::vector<double> D((size_t)p_loc * n_h, 0.0);
-                    for (int s = 0; s < ns; ++s) {
-                        const int c00 = corners[s] & 0xFF, c01 = (corners[s] >> 8) & 0xFF;
-                        const int c10 = (corners[s] >> 16) & 0xFF, c11 = (corners[s] >> 24) & 0xFF;
-                        D[(size_t)c01 * p_loc + s] += 0.5; D[(size_t)c11 * p_loc + s] += 0.5;
-                        D[(size_t)c00 * p_loc + s] -= 0.5; D[(size_t)c10 * p_loc + s] -= 0.5;
-                        D[(size_t)c10 * p_loc + ns + s] += 0.5; D[(size_t)c11 * p_loc + ns + s] += 0.5;
-                        D[(size_t)c00 * p_loc + ns + s] -= 0.5; D[(size_t)c01 * p_loc + ns + s] -= 0.5;
-                    }
-                    std::vector<double> Q;
-                    rk = range_basis(D, p_loc, n_h, Q);
-                    off = (int)h.fac.size();
-                    // F^T = Q^T D (r x n_h) row-major, then Q^T (r x p_loc) row-major
-                    for (int i = 0; i < rk; ++i)
-                        for (int j = 0; j < n_h; ++j) {
-                            double s = 0;
-                            for (int t = 0; t < p_loc; ++t) s += Q[(size_t)i * p_loc + t] * D[(size_t)j * p_loc + t];
-                            h.fac.push_back((float)s);
-                        }
-                    for (int i = 0; i < rk; ++i)
-                        for (int t = 0; t < p_loc; ++t) h.fac.push_back((float)Q[(size_t)i * p_loc + t]);
-                    cache[key] = {rk, off};
-                }
-            }
-            h.rank.push_back(rk);
-            h.fac_off.push_back(off);
-            h.rank_max = std::max(h.rank_max, rk);
             cost.push_back((double)p_loc * 1e6 + (double)n_loc);
         }
     }
@@ -296,8 +184,7 @@ int alloc(letkf_ctx* c, void** p, size_t bytes) {
 void free_all(letkf_ctx* c) {
     void* ptrs[] = {c->X[0], c->X[1], c->Lq, c->Xi, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
                     c->d_status, c->d_frame_bad, c->d_queue, c->tab.own_off, c->tab.own, c->tab.obs_off,
-                    c->tab.obs_sub, c->tab.obs_corner, c->tab.halo_off, c->tab.halo, c->tab.order,
-                    c->tab.rank, c->tab.fac_off, c->tab.fac};
+                    c->tab.obs_sub, c->tab.obs_corner, c->tab.halo_off, c->tab.halo, c->tab.order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->cublas) cublasDestroy(c->cublas);
@@ -313,7 +200,7 @@ void free_all(letkf_ctx* c) {
     c->prof_ev.clear();
 }
 
-int create_impl(const letkf_params* p, letkf_ctx* c) {
+int validate(const letkf_params* p) {
     if (p->n_sub < 1 || p->n_sub > 1024 || p->m < 2 || p->m > 256 || p->dom_sub < 1 || p->halo < 0 ||
         !(p->sigma > 0) || !(std::fabs(p->ar1_a) < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
         p->precision < 0 || p->precision > 2 || p->path < 0 || p->path > 1 || p->q_white < 0 ||
@@ -323,6 +210,38 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     if (p->precision == LETKF_PREC_MIXED && p->path != LETKF_PATH_FUSED) return LETKF_EINVAL;
     if (p->path == LETKF_PATH_PLAIN && !letkf::plain_limits_ok(p->precision, p->m)) return LETKF_EINVAL;
     if (p->dom_sub + 2 * p->halo > 14) return LETKF_EINVAL;  // halo tile must fit the byte-packed corners
+    return LETKF_OK;
+}
+
+// Device bytes held by a context with these parameters once created, from the geometry alone.
+// Mirrors every allocation of create_impl, fused_prepare and init_ensemble.
+size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
+    const size_t eb = p->precision == LETKF_PREC_FP64 ? 8 : 4;
+    const size_t m_pad = eb == 8 ? (size_t)((p->m + 1) / 2) * 2 : (size_t)((p->m + 3) / 4) * 4;
+    const size_t mb_pad = (size_t)((p->m + 7) / 8) * 8;
+    const size_t na = (size_t)h.n_act, n = 2 * na, nd = h.own_off.size() - 1;
+    const size_t row = m_pad * eb;
+    size_t b = 4 * (h.own_off.size() + h.own.size() + h.obs_off.size() + h.obs_sub.size() +
+                    h.obs_corner.size() + h.halo_off.size() + h.halo.size() + h.order.size());
+    b += 2 * n * row + na * row + 4 + 4 + 16;
+    if (p->path == LETKF_PATH_PLAIN) {
+        size_t acc = 0;
+        for (size_t d = 0; d < nd; ++d) acc += 2 * (size_t)(h.obs_off[d + 1] - h.obs_off[d]);
+        b += 4 * nd + std::max<size_t>(acc, 1) * row + std::max<size_t>(acc, 1) * eb;
+        b += nd * p->m * row + nd * row + nd * p->m * row;
+    } else {
+        const size_t vbytes = na * m_pad * 4;
+        b += 2 * vbytes + std::max(na * mb_pad * 2, vbytes);
+    }
+    if (p->q_sqrt) {
+        b += na * na * (p->precision == LETKF_PREC_MIXED ? 2 : eb);
+        b += p->precision == LETKF_PREC_MIXED ? na * mb_pad * 2 : na * row;
+    }
+    return b;
+}
+
+int create_impl(const letkf_params* p, letkf_ctx* c) {
+    if (validate(p)) return LETKF_EINVAL;
     c->n_sub = p->n_sub; c->m = p->m; c->dom_sub = p->dom_sub; c->halo = p->halo;
     c->precision = p->precision; c->path = p->path; c->obs_block = p->obs_block; c->device = p->device;
     c->a = p->ar1_a; c->sigma = p->sigma; c->q_white = p->q_white; c->seed = p->seed;
@@ -332,7 +251,7 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     c->mb_pad = ((c->m + 7) / 8) * 8;
     CU(cudaSetDevice(c->device));
     CU(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
-    build_model(c->host, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo, c->path == LETKF_PATH_FUSED);
+    build_model(c->host, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
     HostModel& h = c->host;
     c->n_act = h.n_act; c->n_subv = h.n_subv; c->n = 2 * h.n_act; c->p = 2 * h.n_subv;
     c->n_dom = (int)h.own_off.size() - 1;
@@ -347,18 +266,13 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     if ((rc = upload(c, h.halo_off, &c->tab.halo_off))) return rc;
     if ((rc = upload(c, h.halo, &c->tab.halo))) return rc;
     if ((rc = upload(c, h.order, &c->tab.order))) return rc;
-    if (c->path == LETKF_PATH_FUSED) {
-        if ((rc = upload(c, h.rank, &c->tab.rank))) return rc;
-        if ((rc = upload(c, h.fac_off, &c->tab.fac_off))) return rc;
-        if ((rc = upload(c, h.fac, &c->tab.fac))) return rc;
-    }
     const size_t row = (size_t)c->m_pad * eb;
     if ((rc = alloc(c, &c->X[0], (size_t)c->n * row))) return rc;
     if ((rc = alloc(c, &c->X[1], (size_t)c->n * row))) return rc;
     if ((rc = alloc(c, &c->V, (size_t)c->n_act * row))) return rc;
     if ((rc = alloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
     if ((rc = alloc(c, (void**)&c->d_frame_bad, sizeof(int)))) return rc;
-    if ((rc = alloc(c, (void**)&c->d_queue, 2 * sizeof(int)))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_queue, 4 * sizeof(int)))) return rc;
     if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     if (cublasSetStream(c->cublas, c->stream) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     if (c->path == LETKF_PATH_PLAIN) {
@@ -429,6 +343,17 @@ int letkf_create(const letkf_params* params, letkf_ctx** out) {
     return LETKF_OK;
 }
 
+int letkf_footprint(const letkf_params* p, unsigned long long* bytes) {
+    if (!p || !bytes) return LETKF_EINVAL;
+    *bytes = 0;
+    if (validate(p)) return LETKF_EINVAL;
+    letkf::HostModel h;
+    build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    if (h.n_act == 0 || h.own_off.size() < 2) return LETKF_EINVAL;
+    *bytes = footprint_bytes(p, h);
+    return LETKF_OK;
+}
+
 int letkf_destroy(letkf_ctx* c) {
     if (!c) return LETKF_OK;
     cudaSetDevice(c->device);
@@ -443,7 +368,7 @@ int letkf_get_info(const letkf_ctx* c, letkf_info* o) {
     if (!c || !o) return LETKF_EINVAL;
     o->n_sub = c->n_sub; o->n_act = c->n_act; o->n_subv = c->n_subv; o->n = c->n; o->p = c->p; o->m = c->m;
     o->n_domains = c->n_dom; o->n_loc_max = c->host.n_loc_max; o->p_loc_max = c->host.p_loc_max;
-    o->rank_max = c->host.rank_max; o->state_bytes = letkf::state_bytes(c);
+    o->state_bytes = letkf::state_bytes(c);
     o->precision = c->precision; o->path = c->path; o->frame = c->frame; o->device_bytes = c->device_bytes;
     o->n_domains_observing = 0;
     o->sum_p_loc = 0;
@@ -594,6 +519,7 @@ const char* letkf_status_string(int s) {
         case LETKF_ESTATE: return "call out of order";
         case LETKF_ENOCONV: return "an eigensolve reached its sweep limit";
         case LETKF_ESCRATCH: return "problem too large for the fixed 16 MiB scratch of letkf_analyze_static";
+        case LETKF_EBUSY: return "refused for now: HBM budget, pending-frame queue or batch slots full";
         default: return "unknown status";
     }
 }

@@ -32,10 +32,6 @@ struct DomainTables {
     int* halo_off = nullptr;    // [n_dom+1] into halo
     int* halo = nullptr;        // valid-actuator indices of the corners of the observed subapertures
     int* order = nullptr;       // [n_dom] processing order, most expensive first
-    // fused path: compressed observation operator per domain
-    int* rank = nullptr;        // [n_dom] rank r of the domain's Fried operator
-    int* fac_off = nullptr;     // [n_dom] float offset of [F^T (r x n_h) ; Q^T (r x p_loc)]
-    float* fac = nullptr;
 };
 
 // Host copy of the geometry and domains.
@@ -46,9 +42,7 @@ struct HostModel {
     std::vector<int> sub_rc, act_rc;         // valid index -> (r, c)
     int n_act = 0, n_subv = 0;
     std::vector<int> own_off, own, obs_off, obs_sub, obs_corner, halo_off, halo, order;
-    std::vector<int> rank, fac_off;
-    std::vector<float> fac;
-    int n_loc_max = 0, p_loc_max = 0, n_h_max = 0, rank_max = 0;
+    int n_loc_max = 0, p_loc_max = 0, n_h_max = 0;
 };
 
 }  // namespace letkf
@@ -86,7 +80,7 @@ struct letkf_ctx {
     // device flags
     int* d_status = nullptr;        // latched status bits
     int* d_frame_bad = nullptr;     // current frame rejected
-    int* d_queue = nullptr;         // work-queue counter of the fused kernel
+    int* d_queue = nullptr;         // fused kernel: [0] work queue, [1] CTAs done, [2] non-finite slope seen
     size_t device_bytes = 0;
     int fused_smem = 0;             // dynamic shared memory of the fused kernel
     int fused_grid = 0;
@@ -134,5 +128,16 @@ int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
 // fused.cu
 int fused_prepare(letkf_ctx* c);
 int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast);
+// One launch of the fused kernel over the next frame of n systems (fused path, same device):
+// their domains form one work queue (`queue`: 4 zeroed ints on the device, reset by the kernel).
+constexpr int FUSED_MAX_BATCH = 32;
+struct FusedFrame {
+    letkf_ctx* c;
+    const void* y;      // device slopes of the frame
+    double sigma;       // <= 0: keep
+    void* xpred;        // device prediction output, or null
+    int with_forecast;
+};
+int fused_batch(const FusedFrame* f, int n, int* queue, cudaStream_t stream);
 
 }  // namespace letkf

@@ -18,6 +18,46 @@ _PREC = {"fp64": _lib.LETKF_PREC_FP64, "fp32": _lib.LETKF_PREC_FP32, "mixed": _l
 _PATH = {"plain": _lib.LETKF_PATH_PLAIN, "fused": _lib.LETKF_PATH_FUSED}
 
 
+def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4, halo: int = 2,
+                obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
+                q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0, p0_sqrt: Optional[np.ndarray] = None,
+                precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1):
+    """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used)."""
+    p = _lib.letkf_params()
+    keep = []
+    p.n_sub = int(n_sub)
+    if sub_valid is not None:
+        sv = np.ascontiguousarray(sub_valid, dtype=np.uint8)
+        keep.append(sv)
+        p.sub_valid = sv.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    p.obstruction = float(obstruction)
+    p.ar1_a = float(ar1_a)
+    p.obs_block = int(obs_block)
+    if q_sqrt is not None:
+        qs = np.ascontiguousarray(q_sqrt, dtype=np.float64)
+        keep.append(qs)
+        p.q_sqrt = qs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.q_white = float(q_white)
+    if p0_sqrt is not None:
+        ps = np.ascontiguousarray(p0_sqrt, dtype=np.float64)
+        keep.append(ps)
+        p.p0_sqrt = ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.sigma = float(sigma)
+    p.m = int(m)
+    p.dom_sub = int(dom_sub)
+    p.halo = int(halo)
+    p.precision = _PREC[precision]
+    p.path = _PATH[path]
+    p.seed = int(seed)
+    return p, keep
+
+
+def footprint(**kw) -> int:
+    """Device bytes a context with these parameters (as for LETKF) holds once created."""
+    p, keep = make_params(**kw)
+    return _lib.letkf_footprint(p)
+
+
 class LETKF:
     """One adaptive-optics system's local ETKF, resident on one GPU."""
 
@@ -33,32 +73,10 @@ class LETKF:
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = torch.device("cuda", dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        p = _lib.letkf_params()
-        p.n_sub = int(n_sub)
-        self._keep = []
-        if sub_valid is not None:
-            sv = np.ascontiguousarray(sub_valid, dtype=np.uint8)
-            self._keep.append(sv)
-            p.sub_valid = sv.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
-        p.obstruction = float(obstruction)
-        p.ar1_a = float(ar1_a)
-        p.obs_block = int(obs_block)
-        if q_sqrt is not None:
-            qs = np.ascontiguousarray(q_sqrt, dtype=np.float64)
-            self._keep.append(qs)
-            p.q_sqrt = qs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        p.q_white = float(q_white)
-        if p0_sqrt is not None:
-            ps = np.ascontiguousarray(p0_sqrt, dtype=np.float64)
-            self._keep.append(ps)
-            p.p0_sqrt = ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        p.sigma = float(sigma)
-        p.m = int(m)
-        p.dom_sub = int(dom_sub)
-        p.halo = int(halo)
-        p.precision = _PREC[precision]
-        p.path = _PATH[path]
-        p.seed = int(seed)
+        p, keep = make_params(n_sub=n_sub, m=m, ar1_a=ar1_a, sigma=sigma, dom_sub=dom_sub, halo=halo,
+                              obstruction=obstruction, sub_valid=sub_valid, q_sqrt=q_sqrt, q_white=q_white,
+                              p0_sqrt=p0_sqrt, precision=precision, path=path, seed=seed, obs_block=obs_block)
+        self._keep = keep
         p.device = dev
         p.stream = self.stream.cuda_stream
         with torch.cuda.device(self.device):

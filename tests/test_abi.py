@@ -3,6 +3,8 @@
 import ctypes
 import os
 
+import numpy as np
+
 import pytest
 
 from paper_1310_5954_gb300 import _lib
@@ -28,7 +30,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for s in range(-8, 1):
+    for s in range(-9, 1):
         assert _lib.letkf_status_string(s) not in ("", "unknown status")
     assert _lib.letkf_status_string(-99) == "unknown status"
 
@@ -61,3 +63,32 @@ def test_null_arguments(lib):
     assert lib.letkf_sync(None) == _lib.LETKF_EINVAL
     assert lib.letkf_step(None, None, 0.0, None) == _lib.LETKF_EINVAL
     assert lib.letkf_create(None, None) == _lib.LETKF_EINVAL
+
+
+def test_footprint_on_the_host(lib):
+    from paper_1310_5954_gb300 import footprint
+    base = dict(n_sub=8, m=20, ar1_a=0.99, sigma=0.1, dom_sub=4, halo=1, precision="mixed", path="fused")
+    f0 = footprint(**base, q_white=0.1)
+    n_act = 69                                  # 8x8 circular pupil (oracle geometry pins)
+    L = np.eye(n_act)
+    f1 = footprint(**base, q_sqrt=L)
+    # a dense noise factor adds the BF16 factor and the BF16 normals (rows of m rounded up to 8)
+    assert f1 - f0 == n_act * n_act * 2 + n_act * 24 * 2
+    # per member: the two ensemble buffers (2 x 2 n_act rows), the perturbation buffer (n_act)
+    # and the fused path's two noise buffers and normals (3 x n_act), FP32
+    f2 = footprint(**dict(base, m=40), q_white=0.1)
+    assert f2 - f0 == (4 + 1 + 3) * n_act * 20 * 4
+    with pytest.raises(_lib.LETKFError):
+        footprint(**dict(base, m=1))
+
+
+def test_server_rejects_invalid_parameters(lib):
+    out = ctypes.c_void_p(99)
+    for bad in [dict(max_systems=0), dict(slots=9), dict(max_pending=0), dict(max_batch=33)]:
+        p = _lib.letkf_server_params()
+        p.device, p.max_systems, p.slots, p.max_pending, p.max_batch = 0, 4, 2, 8, 8
+        for k, v in bad.items():
+            setattr(p, k, v)
+        assert lib.letkf_server_create(ctypes.byref(p), ctypes.byref(out)) == _lib.LETKF_EINVAL
+        assert out.value is None
+    assert lib.letkf_server_destroy(None) == _lib.LETKF_OK

@@ -125,10 +125,21 @@ def test_fused_empty_domains_nonfinite_and_resume():
     before = before.clone()
     bad = yv.copy()
     bad[1] = np.inf
-    f.step(_t(bad))
+    xp = f.step(_t(bad))
     assert f.sync() == _lib.LETKF_ENONFINITE
     after, fr2 = f.get_state()
     assert torch.equal(before, after) and fr2 == fr + 1
+    # the prediction of a rejected frame is the mean of the unchanged first instant
+    assert torch.allclose(xp, before[:g.n_act].mean(1), rtol=0, atol=1e-6)
+    # analysis of a rejected frame, then its forecast: both leave the state as it was
+    f.analyze(_t(bad))
+    f.forecast()
+    assert f.sync() == _lib.LETKF_ENONFINITE
+    after2, _ = f.get_state()
+    assert torch.equal(before, after2)
+    # and the next good frame runs
+    f.step(_t(yv))
+    assert f.sync() == 0
     f.close()
 
 
