@@ -53,7 +53,10 @@ struct SysDesc {
     int* frame_bad;      // frame-level rejection flag, written at the end of the launch
     int* dom_bad;        // set by any domain that meets a non-finite slope; reset at the end
     unsigned long long seed;
-    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, item0;
+    float* scratch;      // dual form: per-CTA halo anomalies (scratch_stride floats per CTA)
+    int scratch_stride;
+    int dual;            // analysis in observation space (m >= 128)
+    int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, RA, item0;
     float inv_sigma, a, q_white;
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
@@ -228,7 +231,7 @@ __device__ void fetch_item(const FusedBatch& B, Ctrl* ctl, unsigned char* smem, 
     const int d = A.tab.order[g - A.item0];
     ctl->sys = s;
     ctl->dom = d;
-    if (A.tab.obs_off[d + 1] > A.tab.obs_off[d] && A.off_big <= busy_from) {
+    if (!A.dual && A.tab.obs_off[d + 1] > A.tab.obs_off[d] && A.off_big <= busy_from) {
         issue_loads(A, d, smem, &ctl->bar_load);
         ctl->loaded = 1;
     }
@@ -266,6 +269,522 @@ __device__ void finish_batch(const FusedBatch& B) {
         B.queue[1] = 0;
         __threadfence();
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dual analysis, for ensembles wider than one MMA tile (m >= 128): every matrix lives in the
+// p-dimensional observation space of the domain (p = p_loc <= 128).  With S = Y'/sigma (p x m),
+// d the innovation / sigma, c = m - 1, K = S S^T and Z = (I + K/c)^(-1/2):
+//   w_bar = [(m-1)I + G]^-1 S^T d = S^T (cI + K)^-1 d = S^T u,   u = Z^2 d / c,
+//   T = (I + G/c)^(-1/2) = I - W^T (I + Z)^-1 W,   W = Z S / sqrt(c)
+// (on an eigenvector of G with eigenvalue l: z = (1 + l/c)^(-1/2) and 1 - (l/c) z^2 / (1 + z) = z),
+// so X'_E T = X'_E - (X'_E W^T) ((I + Z)^-1 W).  W has singular values sqrt(l / (c + l)) <= 1:
+// unlike S^T H S / c with H = Z^2 (I + Z)^-1, whose factors' rounding S would amplify by up to
+// l / c, nothing here grows with the conditioning.  Z comes from the same coupled Newton-Schulz
+// iteration as the m x m form, (I + Z)^-1 from Newton's iteration for the inverse (the
+// eigenvalues of I + Z lie in (1, 2]), and u is refined against the exact operator.  Halo
+// anomalies stay in a per-CTA global scratch (L2-resident), so shared memory holds only the
+// operands of one product at a time.
+__device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32_t tbase, uint32_t* ph_mma_io,
+                                          int d) {
+    const SysDesc A = ctl->sd;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = 32 * (warp & 3) + lane, hh = warp >> 2;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    uint32_t ph_mma = *ph_mma_io;
+    float* vec = reinterpret_cast<float*>(smem + A.off_vec);
+    float* xh_mean = vec;            // 256 (halo actuators)
+    float* dvec = vec + 256;         // 128 innovation / sigma per observed slope
+    float* uvp = vec + 384;          // 128 u
+    float* vr = vec + 512;           // 128
+    float* vv = vec + 640;           // 128
+    float* vtmp = vec + 768;         // 2 x 128
+    float* wbar = vec + 1024;        // 256 mean weights (members)
+    float* xe_mean = vec + 1280;     // 128 (own rows)
+    float* uvec = vec + 1408;        // 128 mean update of each own row
+    unsigned char* big = smem + A.off_big;
+    const int m = A.m, NP = A.NP, MP = A.KP, RA = A.RA;
+    const float c = (float)(m - 1);
+    float* Xs = A.scratch + (size_t)blockIdx.x * A.scratch_stride;
+    const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
+    const int o0 = A.tab.obs_off[d], n_obs = A.tab.obs_off[d + 1] - o0;
+    const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
+    const int P = 2 * n_obs;
+    const int n_e = A.with_forecast ? n_own : 2 * n_own;
+    // p-space matrices: NP x NP, this thread's TMEM lane `row`, columns col0 .. col0 + NP/2
+    const int half = NP / 2, nq = half / 8, col0 = hh * half;
+    const uint32_t tl = tbase + lane_off + (uint32_t)col0;
+    unsigned char* Yh = big;
+    unsigned char* Yl = big + A.sz_op;
+    unsigned char* Zh = big + 2 * A.sz_op;
+    unsigned char* Zl = big + 3 * A.sz_op;
+    unsigned char* Th = big + 4 * A.sz_op;
+    unsigned char* Tl = big + 5 * A.sz_op;
+    auto mma_wait = [&]() -> bool {
+        if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) return false;
+        ph_mma ^= 1;
+        tc_fence_after();
+        return true;
+    };
+    auto to_mma = [&]() {    // operands written by the threads -> visible to the tensor core
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    };
+
+    // ---- halo anomalies of the observed instant (FP32) into the scratch
+    for (int j = warp; j < n_h; j += FT / 32) {
+        const float* x = A.X + (size_t)(A.row_obs + A.tab.halo[h0 + j]) * A.m_pad;
+        float sm_ = 0.f;
+        for (int i = lane; i < m; i += 32) sm_ += x[i];
+        sm_ = warp_sum(sm_);
+        const float mu = sm_ / (float)m;
+        for (int i = lane; i < m; i += 32) Xs[(size_t)j * A.m_pad + i] = x[i] - mu;
+        if (lane == 0) xh_mean[j] = mu;
+    }
+    __syncthreads();
+    auto slope_at = [&](int k, int i) -> float {    // S[k][i], k = 2 s + direction
+        const int pc = A.tab.obs_corner[o0 + (k >> 1)];
+        const float a00 = Xs[(size_t)(pc & 0xFF) * A.m_pad + i];
+        const float a01 = Xs[(size_t)((pc >> 8) & 0xFF) * A.m_pad + i];
+        const float a10 = Xs[(size_t)((pc >> 16) & 0xFF) * A.m_pad + i];
+        const float a11 = Xs[(size_t)((pc >> 24) & 0xFF) * A.m_pad + i];
+        const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+        return sl * A.inv_sigma;
+    };
+    for (int k = tid; k < P; k += FT) {             // innovation d / sigma
+        const int pc = A.tab.obs_corner[o0 + (k >> 1)];
+        const float a00 = xh_mean[pc & 0xFF], a01 = xh_mean[(pc >> 8) & 0xFF];
+        const float a10 = xh_mean[(pc >> 16) & 0xFF], a11 = xh_mean[(pc >> 24) & 0xFF];
+        const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+        const int sub = A.tab.obs_sub[o0 + (k >> 1)];
+        const float yv = (k & 1) == 0 ? A.y[sub] : A.y[A.n_subv + sub];
+        dvec[k] = (yv - sl) * A.inv_sigma;
+    }
+    // S as an NP x MP operand (rows: slopes, K: members)
+    auto write_S = [&](unsigned char* hi, unsigned char* lo) {
+        for (int t = tid; t < NP * (MP >> 3); t += FT) {
+            const int k = t % NP, ic = t / NP;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = ic * 8 + u;
+                v[u] = (k < P && i < m) ? slope_at(k, i) : 0.f;
+            }
+            store8(hi, lo, k, ic * 8, MP, v, true);
+        }
+    };
+    unsigned char* Sg_h = big;
+    unsigned char* Sg_l = big + A.sz_opg;
+    write_S(Sg_h, Sg_l);
+    to_mma();
+    if (tid == 0) {
+        tc_fence_after();
+        issue_product(tbase + TM_G, Sg_h, Sg_l, Sg_h, Sg_l, MP, NP, A.gram_terms, 0);   // K = S S^T
+        mma_commit(&ctl->bar_mma);
+    }
+    if (!mma_wait()) return false;
+    auto read_fro = [&]() -> float {
+        float fr = 0.f;
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            float g[8];
+            tmem_ld8(tl + TM_G + 8 * q8, g);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (row < P && col0 + 8 * q8 + u < P) fr += g[u] * g[u];
+        }
+        return block_sum(ctl, fr);
+    };
+    float fro = read_fro();
+    if (A.gram_terms < 3 && 1.f + sqrtf(fro) / c > A.s_split) {
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_G, Sg_h, Sg_l, Sg_h, Sg_l, MP, NP, 3, 0, 1);
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!mma_wait()) return false;
+        fro = read_fro();
+    }
+    const float s_scale = 1.f + sqrtf(fro) / c;
+    const float inv_cs = 1.f / (c * s_scale);
+    // ---- Z = ((I + K/c)/s)^(-1/2) by the coupled Newton-Schulz iteration (dimension P)
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {
+        float g[8], yv[8], zv[8];
+        tmem_ld8(tl + TM_G + 8 * q8, g);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = col0 + 8 * q8 + u;
+            const bool in = row < P && j < P;
+            const float id = (row == j) ? 1.f : 0.f;
+            yv[u] = in ? (id + g[u] / c) / s_scale : 0.f;
+            zv[u] = in ? id : 0.f;
+        }
+        if (row < NP) {
+            store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+            store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
+        }
+    }
+    to_mma();
+    bool z_in_tmem = false;
+    float rn_prev = 3.0e38f;
+    int it = 0;
+    for (; it < A.max_it; ++it) {
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_P, Zh, Zl, Yh, Yl, NP, NP, 3, 1);
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!mma_wait()) return false;
+        float r2 = 0.f;
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            float pv[8], tv[8];
+            tmem_ld8(tl + TM_P + 8 * q8, pv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = col0 + 8 * q8 + u;
+                const bool in = row < P && j < P;
+                const float id = (row == j) ? 1.f : 0.f;
+                const float rr = id - pv[u];
+                if (in) r2 += rr * rr;
+                tv[u] = in ? 1.5f * id - 0.5f * pv[u] : 0.f;
+            }
+            if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
+        }
+        r2 = block_sum(ctl, r2);
+        const float rn = sqrtf(r2);
+        const bool conv = rn < 2e-6f * (float)P || (rn < 2e-2f && rn > 0.6f * rn_prev);
+        rn_prev = rn;
+        if (conv) break;
+        to_mma();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
+            issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!mma_wait()) return false;
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            float yv[8], zv[8];
+            tmem_ld8(tl + TM_Y + 8 * q8, yv);
+            tmem_ld8(tl + TM_Z + 8 * q8, zv);
+            if (row < NP) {
+                store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
+            }
+        }
+        z_in_tmem = true;
+        to_mma();
+    }
+    if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    auto zrow = [&](int q8, float (&zv)[8]) {       // 8 columns of this thread's half-row of Z_ns
+        if (z_in_tmem) {
+            tmem_ld8(tl + TM_Z + 8 * q8, zv);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) zv[u] = (row == col0 + 8 * q8 + u && row < P) ? 1.f : 0.f;
+        }
+    };
+    auto zmatvec = [&](const float* x_in, float* y_out) {   // y = Z_ns x over the first P entries
+        float part = 0.f;
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            float zv[8];
+            zrow(q8, zv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (col0 + 8 * q8 + u < P) part += zv[u] * x_in[col0 + 8 * q8 + u];
+        }
+        vtmp[hh * 128 + row] = part;
+        __syncthreads();
+        if (hh == 0) y_out[row] = (row < P) ? vtmp[row] + vtmp[128 + row] : 0.f;
+        __syncthreads();
+    };
+    auto st_times = [&](const float* u_in, float* w_out) {    // w = S^T u (members)
+        for (int i = tid; i < m; i += FT) {
+            float acc = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < P; ++k) acc += slope_at(k, i) * u_in[k];
+            w_out[i] = acc;
+        }
+        __syncthreads();
+    };
+    // ---- mean weights: u = Z_ns (Z_ns d) / (c s), refined against the exact FP32 slopes;
+    //      w_bar = S^T u
+    zmatvec(dvec, vv);
+    zmatvec(vv, uvp);
+    if (hh == 0) uvp[row] = row < P ? uvp[row] * inv_cs : 0.f;
+    __syncthreads();
+    const int n_ref = s_scale > A.s_split ? 2 : 1;
+    for (int ref = 0; ref < n_ref; ++ref) {
+        st_times(uvp, wbar);                                   // S^T u
+        for (int k = warp; k < P; k += FT / 32) {              // rho = d - c u - S (S^T u)
+            float part = 0.f;
+            for (int i = lane; i < m; i += 32) part += slope_at(k, i) * wbar[i];
+            part = warp_sum(part);
+            if (lane == 0) vr[k] = dvec[k] - c * uvp[k] - part;
+        }
+        __syncthreads();
+        zmatvec(vr, vv);
+        zmatvec(vv, vr);
+        if (hh == 0 && row < P) uvp[row] += vr[row] * inv_cs;
+        __syncthreads();
+    }
+    st_times(uvp, wbar);
+    // ---- (I + Z)^-1, Z = Z_ns / sqrt(s), by Newton's iteration X <- X (2I - (I + Z) X) from
+    //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G
+    const float rs = rsqrtf(s_scale);
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {               // M = I + Z into Y's buffers, X_0 into T's
+        float zv[8], mv[8], xv[8];
+        zrow(q8, zv);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = col0 + 8 * q8 + u;
+            const bool in = row < P && j < P;
+            const float id = (row == j) ? 1.f : 0.f;
+            mv[u] = in ? id + zv[u] * rs : 0.f;
+            xv[u] = in ? (2.f / 3.f) * id : 0.f;
+        }
+        if (row < NP) {
+            store8(Yh, Yl, row, col0 + 8 * q8, NP, mv, true);
+            store8(Th, Tl, row, col0 + 8 * q8, NP, xv, true);
+        }
+    }
+    to_mma();
+    bool x_in_tmem = false;
+    for (int k = 0; k < 6; ++k) {
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_P, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Q = M X
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!mma_wait()) return false;
+        float r2 = 0.f;
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            float qv[8], rv[8];
+            tmem_ld8(tl + TM_P + 8 * q8, qv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = col0 + 8 * q8 + u;
+                const bool in = row < P && j < P;
+                const float id = (row == j) ? 1.f : 0.f;
+                if (in) r2 += (id - qv[u]) * (id - qv[u]);
+                rv[u] = in ? 2.f * id - qv[u] : 0.f;
+            }
+            if (row < NP) store8(Zh, Zl, row, col0 + 8 * q8, NP, rv, true);   // Z's operand is not needed
+        }
+        r2 = block_sum(ctl, r2);
+        if (sqrtf(r2) < 1e-6f * (float)P) break;
+        to_mma();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_product(tbase + TM_G, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // X R
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!mma_wait()) return false;
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            float xv[8];
+            tmem_ld8(tl + TM_G + 8 * q8, xv);
+            if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, xv, true);
+        }
+        x_in_tmem = true;
+        to_mma();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // ---- W = Z S / sqrt(c) (NP x MP).  T = I - W^T (I + Z)^-1 W: W has singular values
+    //      sqrt(l / (c + l)) <= 1, so the rounding of its factors is not amplified by S.
+    unsigned char* Zt_h = big;
+    unsigned char* Zt_l = big + A.sz_op;
+    unsigned char* Wh = big + A.sz_a;
+    unsigned char* Wl = big + A.sz_a + A.sz_opg;
+    const float zscale = rs * rsqrtf(c);
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {
+        float zv[8];
+        zrow(q8, zv);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) zv[u] = (row < P && col0 + 8 * q8 + u < P) ? zv[u] * zscale : 0.f;
+        if (row < NP) store8(Zt_h, Zt_l, row, col0 + 8 * q8, NP, zv, true);
+    }
+    write_S(Wh, Wl);
+    to_mma();
+    if (tid == 0) {
+        tc_fence_after();
+        issue_product(tbase + TM_Y, Zt_h, Zt_l, Wh, Wl, NP, MP, 3, 1);    // W = (Z / sqrt(c)) S
+        mma_commit(&ctl->bar_mma);
+    }
+    // own rows: member mean and the mean update X'_E w_bar (FP64 sums), under the product
+    for (int e = warp; e < n_e; e += FT / 32) {
+        const int r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
+        const float* x = A.X + (size_t)r * A.m_pad;
+        float sm_ = 0.f;
+        for (int i = lane; i < m; i += 32) sm_ += x[i];
+        sm_ = warp_sum(sm_);
+        const float mu = sm_ / (float)m;
+        double u = 0.0;
+        for (int i = lane; i < m; i += 32) u += (double)(x[i] - mu) * (double)wbar[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (lane == 0) {
+            xe_mean[e] = mu;
+            uvec[e] = (float)u;
+        }
+    }
+    if (!mma_wait()) return false;
+    const int mhalf = MP / 2, mq = mhalf / 8, mcol0 = hh * mhalf;
+    const uint32_t tlm = tbase + lane_off + (uint32_t)mcol0;
+#pragma unroll 1
+    for (int q8 = 0; q8 < mq; ++q8) {               // W -> operand over S
+        float wv[8];
+        tmem_ld8(tlm + TM_Y + 8 * q8, wv);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wv[u] = (row < P && mcol0 + 8 * q8 + u < m) ? wv[u] : 0.f;
+        if (row < NP) store8(Wh, Wl, row, mcol0 + 8 * q8, MP, wv, true);
+    }
+    unsigned char* A1h = big;                       // X'_E (RA x MP) over Z's operand
+    unsigned char* A1l = big + RA * MP * 2;
+    for (int t = tid; t < RA * (MP >> 3); t += FT) {
+        const int e = t % RA, kc = t / RA;
+        float v[8];
+        int r = 0;
+        if (e < n_e) r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = kc * 8 + u;
+            v[u] = (e < n_e && k < m) ? A.X[(size_t)r * A.m_pad + k] - xe_mean[e] : 0.f;
+        }
+        store8(A1h, A1l, e, kc * 8, MP, v, A.tr_terms > 1);
+    }
+    to_mma();
+    if (tid == 0) {
+        tc_fence_after();
+        issue_product(tbase + TM_P, A1h, A1l, Wh, Wl, MP, NP, A.tr_terms, 0);   // P1 = X'_E W^T
+        mma_commit(&ctl->bar_mma);
+    }
+    if (!mma_wait()) return false;
+    unsigned char* Xh_op = big;                     // (I + Z)^-1 operand over A1
+    unsigned char* Xl_op = big + A.sz_op;
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {
+        float xv[8];
+        if (x_in_tmem) {
+            tmem_ld8(tl + TM_G + 8 * q8, xv);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xv[u] = (row == col0 + 8 * q8 + u) ? 2.f / 3.f : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = (row < P && col0 + 8 * q8 + u < P) ? xv[u] : 0.f;
+        if (row < NP) store8(Xh_op, Xl_op, row, col0 + 8 * q8, NP, xv, true);
+    }
+    to_mma();
+    if (tid == 0) {
+        tc_fence_after();
+        issue_product(tbase + TM_Y, Xh_op, Xl_op, Wh, Wl, NP, MP, 3, 1);   // XW = (I + Z)^-1 W
+        mma_commit(&ctl->bar_mma);
+    }
+    if (!mma_wait()) return false;
+    unsigned char* A2h = big;                       // P1 (RA x NP) over X's operand
+    unsigned char* A2l = big + RA * NP * 2;
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {
+        float pv[8];
+        tmem_ld8(tl + TM_P + 8 * q8, pv);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) pv[u] = (row < n_e && col0 + 8 * q8 + u < P) ? pv[u] : 0.f;
+        if (row < RA) store8(A2h, A2l, row, col0 + 8 * q8, NP, pv, A.tr_terms > 1);
+    }
+#pragma unroll 1
+    for (int q8 = 0; q8 < mq; ++q8) {               // XW -> operand over W
+        float wv[8];
+        tmem_ld8(tlm + TM_Y + 8 * q8, wv);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wv[u] = (row < P && mcol0 + 8 * q8 + u < m) ? wv[u] : 0.f;
+        if (row < NP) store8(Wh, Wl, row, mcol0 + 8 * q8, MP, wv, true);
+    }
+    to_mma();
+    if (tid == 0) {
+        tc_fence_after();
+        issue_product(tbase + TM_Y, A2h, A2l, Wh, Wl, NP, MP, A.tr_terms, 1);   // P3 = P1 (XW)
+        mma_commit(&ctl->bar_mma);
+    }
+    if (!mma_wait()) return false;
+    // ---- epilogue: X_a = X + X'_E w_bar - (P3 - row mean of P3); forecast; prediction
+    const bool mine = row < n_e;
+    int grow = 0, jact = 0;
+    if (mine) {
+        jact = row < n_own ? A.tab.own[e0 + row] : A.tab.own[e0 + row - n_own];
+        grow = row < n_own ? jact : A.n_act + jact;
+    }
+    {
+        float part = 0.f;
+#pragma unroll 1
+        for (int q8 = 0; q8 < mq; ++q8) {
+            float dv[8];
+            tmem_ld8(tlm + TM_Y + 8 * q8, dv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (mcol0 + 8 * q8 + u < m) part += dv[u];
+        }
+        vtmp[hh * 128 + row] = part;
+        __syncthreads();
+    }
+    const float p3mean = mine ? (vtmp[row] + vtmp[128 + row]) / (float)m : 0.f;
+    const float shift = mine ? uvec[row] : 0.f;
+    __syncthreads();
+    float psum = 0.f;
+#pragma unroll 1
+    for (int q8 = 0; q8 < mq; ++q8) {
+        float dv[8];
+        tmem_ld8(tlm + TM_Y + 8 * q8, dv);
+        if (!mine) continue;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = mcol0 + 8 * q8 + u;
+            if (j < m) {
+                const float xa = A.X[(size_t)grow * A.m_pad + j] + shift - (dv[u] - p3mean);
+                if (A.with_forecast) {
+                    float v = 0.f;
+                    if (A.vmode == 0) {
+                        v = A.V[(size_t)jact * A.m_pad + j];
+                    } else if (A.vmode == 1) {
+                        float zz[4];
+                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
+                        v = A.q_white * zz[jact & 3];
+                    }
+                    const float n1 = A.a * xa + v;
+                    A.Xo[(size_t)jact * A.m_pad + j] = n1;
+                    A.Xo[(size_t)(A.n_act + jact) * A.m_pad + j] = xa;
+                    psum += n1;
+                } else {
+                    A.Xo[(size_t)grow * A.m_pad + j] = xa;
+                }
+            }
+        }
+    }
+    if (A.with_forecast) {
+        vtmp[hh * 128 + row] = psum;
+        __syncthreads();
+        if (hh == 0 && mine && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    *ph_mma_io = ph_mma;
+    return true;
 }
 
 __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ FusedBatch B) {
@@ -350,7 +869,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             __syncthreads();
             continue;
         }
-        if (tid == 0 && !ctl->loaded) issue_loads(A, d, smem, &ctl->bar_load);
+        if (tid == 0 && !A.dual && !ctl->loaded) issue_loads(A, d, smem, &ctl->bar_load);
         // ---- frame ingest: a non-finite slope in this domain's observation region rejects the
         //      system's frame (its state is restored when the launch ends)
         int nonfinite = 0;
@@ -359,6 +878,20 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             if (!isfinite(A.y[sub]) || !isfinite(A.y[A.n_subv + sub])) nonfinite = 1;
         }
         const bool dom_bad = __syncthreads_or(nonfinite) != 0;
+        if (A.dual) {
+            if (dom_bad) {
+                if (tid == 0) {
+                    atomicExch(A.dom_bad, 1);
+                    atomicOr(A.status, ST_NONFINITE);
+                }
+            } else if (!analyse_dual(ctl, smem, tbase, &ph_mma, d)) {
+                break;
+            }
+            __syncthreads();
+            if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
+            __syncthreads();
+            continue;
+        }
         // ---- 1. the halo rows of the observed instant and the own rows
         if (!wait_all(ctl, &ctl->bar_load, ph_load, A.status)) break;
         ph_load ^= 1;
@@ -645,7 +1178,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             }
         }
         __syncthreads();
-        const int RA = A.sz_a / (NP * 2);
+        const int RA = A.RA;
         for (int t = tid; t < RA * (NP >> 3); t += FT) {
             const int e = t % RA, kc = t / RA;
             float v[8];
@@ -827,16 +1360,38 @@ struct FusedLayout {
     int NP, KP, RA, sz_op, sz_opg, sz_a, off_vec, off_xe, off_xh, off_big, total;
 };
 
+// Ensembles of m >= 128 members do not fit one 128-row MMA tile: they take the dual form.
+bool uses_dual(int m) { return m + 1 > MT; }
+
 FusedLayout fused_layout(const letkf_ctx* c) {
     const HostModel& h = c->host;
     FusedLayout L;
+    L.off_vec = 1024;
+    if (uses_dual(c->m)) {
+        // p-space matrices NP x NP, slopes x members NP x KP, own rows RA
+        L.NP = std::max(16, round_up(h.p_loc_max, 16));
+        L.KP = round_up(c->m, 16);
+        L.RA = round_up(std::max(h.n_loc_max, 1), 16);
+        // buffers: sz_op per p x p operand half, sz_opg per p x m half; below sz_a the transform's
+        // left operands (Z, X'_E, (I + Z)^-1, X'_E W^T), from sz_a the p x m ones (S, W, XW)
+        L.sz_op = round_up(L.NP * L.NP * 2, 1024);
+        L.sz_opg = round_up(L.NP * L.KP * 2, 1024);
+        L.sz_a = round_up(std::max(std::max(2 * L.RA * L.KP * 2, 2 * L.sz_op), 2 * L.RA * L.NP * 2), 1024);
+        L.off_xe = L.off_xh = L.off_big = L.off_vec + 8192;
+        // each phase's buffers plus the rows a 128-row MMA reads past its left operand
+        const int gram = std::max(2 * L.sz_opg, L.sz_opg + MT * L.KP * 2);
+        const int ns = std::max(6 * L.sz_op, 5 * L.sz_op + MT * L.NP * 2);
+        const int tr = std::max(std::max(L.sz_a + 2 * L.sz_opg, L.RA * L.KP * 2 + MT * L.KP * 2),
+                                std::max(L.sz_op + MT * L.NP * 2, L.RA * L.NP * 2 + MT * L.NP * 2));
+        L.total = L.off_big + round_up(std::max(gram, std::max(ns, tr)), 1024);
+        return L;
+    }
     L.NP = round_up(c->m + 1, 16);
     L.KP = std::max(16, round_up(h.p_loc_max, 16));
     L.RA = std::min(MT, round_up(std::max(L.NP, h.n_loc_max), 16));
     L.sz_op = round_up(L.NP * L.NP * 2, 1024);
     L.sz_opg = round_up(L.NP * L.KP * 2, 1024);
     L.sz_a = L.RA * L.NP * 2;          // a multiple of 512: keeps 16-byte alignment
-    L.off_vec = 1024;
     L.off_xe = L.off_vec + 8192;
     const int xe_bytes = round_up(std::max(h.n_loc_max, 1) * c->m_pad * 4, 1024);
     L.off_xh = L.off_xe + xe_bytes;
@@ -852,12 +1407,19 @@ FusedLayout fused_layout(const letkf_ctx* c) {
 
 int fused_prepare(letkf_ctx* c) {
     const HostModel& h = c->host;
-    if (c->m + 1 > MT) return LETKF_EINVAL;
     const FusedLayout L = fused_layout(c);
-    if (L.NP > MT || L.KP > MT) return LETKF_EINVAL;   // m <= 127, at most 128 slopes per domain
+    c->dual = uses_dual(c->m) ? 1 : 0;
+    // at most 128 slopes per domain; m <= 127 (one tile) or, in the dual form, m <= 256
+    if (L.NP > MT || L.KP > (c->dual ? 2 * MT : MT) || L.RA > MT) return LETKF_EINVAL;
     if (L.total > 227 * 1024) return LETKF_EINVAL;
     if (h.n_h_max > 255 || h.n_loc_max > MT) return LETKF_EINVAL;
     c->fused_smem = L.total;
+    if (c->dual) {
+        c->scratch_stride = std::max(h.n_h_max, 1) * c->m_pad;
+        const size_t sb = (size_t)c->sms * c->scratch_stride * 4;
+        if (cudaMalloc(&c->scratch, sb) != cudaSuccess) return LETKF_ENOMEM;
+        c->device_bytes += sb;
+    }
     static_assert(sizeof(FusedBatch) < 32000, "kernel parameters too large");
     if (cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
         return LETKF_ECUDA;
@@ -948,6 +1510,10 @@ int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
     const FusedLayout L = fused_layout(c);
     S->NP = L.NP;
     S->KP = L.KP;
+    S->RA = L.RA;
+    S->dual = c->dual;
+    S->scratch = static_cast<float*>(c->scratch);
+    S->scratch_stride = c->scratch_stride;
     S->inv_sigma = (float)(1.0 / c->sigma);
     S->a = (float)c->a;
     S->q_white = (float)c->q_white;

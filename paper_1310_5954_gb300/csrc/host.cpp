@@ -195,6 +195,7 @@ void free_all(letkf_ctx* c) {
         if (c->ev_v_used[b]) cudaEventDestroy(c->ev_v_used[b]);
     }
     if (c->Xi_side) cudaFree(c->Xi_side);
+    if (c->scratch) cudaFree(c->scratch);
     if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
@@ -232,6 +233,11 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
     } else {
         const size_t vbytes = na * m_pad * 4;
         b += 2 * vbytes + std::max(na * mb_pad * 2, vbytes);
+        if (p->m + 1 > 128) {   // dual form: per-CTA halo anomalies
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) sms = 0;
+            b += (size_t)sms * std::max(h.n_h_max, 1) * m_pad * 4;
+        }
     }
     if (p->q_sqrt) {
         b += na * na * (p->precision == LETKF_PREC_MIXED ? 2 : eb);

@@ -84,6 +84,9 @@ struct letkf_ctx {
     size_t device_bytes = 0;
     int fused_smem = 0;             // dynamic shared memory of the fused kernel
     int fused_grid = 0;
+    int dual = 0;                   // fused analysis in observation space (m >= 128)
+    void* scratch = nullptr;        // dual form: per-CTA halo anomalies, SMs x scratch_stride floats
+    int scratch_stride = 0;
     // fused path: process noise of the next frame drawn on a side stream while the current
     // frame's kernel runs (double-buffered; v_frame[b] = frame whose draw buffer b holds)
     cudaStream_t side = nullptr;

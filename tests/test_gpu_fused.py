@@ -54,6 +54,47 @@ def test_single_frame_analysis(prec, name, frames):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("name,m", [("tiny-8x8", 150), ("vlt-40x40", 200), ("elt-80x80", 256)])
+def test_dual_form_single_frame_analysis(prec, name, m):
+    """Ensembles of m >= 128 members take the observation-space form of the analysis
+    (K = S S^T, T = I - S^T Z^2 (I + Z)^-1 S / c); same bounds as the m x m form."""
+    y, _ = slopes(name, 3)
+    f = gpu_filter(name, prec, "fused", m=m)
+    o = oracle_filter(name, m=m)
+    tm, te = TOL[prec]
+    for k in range(2):
+        xf = o.X.astype(np.float32).astype(np.float64)
+        f.set_state(_t(xf), k)
+        o.X = xf.copy()
+        f.analyze(_t(y[k]))
+        o.analyze(y[k].astype(np.float32).astype(np.float64))
+        xa, _ = f.get_state()
+        xa = xa.cpu().numpy().astype(np.float64)
+        assert rel(xa.mean(1), o.X.mean(1)) < tm, (k, rel(xa.mean(1), o.X.mean(1)))
+        assert rel(xa, o.X) < te, (k, rel(xa, o.X))
+        f.forecast()
+        o.forecast()
+    assert f.sync() == 0
+    f.close()
+
+
+def test_dual_form_free_running_residual():
+    """m = 200 on the 40x40 system: 40 free-running frames from the cold start track the
+    oracle's prediction (relative L2 of x_hat(k+1|k) per frame)."""
+    y, _ = slopes("vlt-40x40", 40)
+    f = gpu_filter("vlt-40x40", "mixed", "fused", m=200)
+    o = oracle_filter("vlt-40x40", m=200)
+    worst = 0.0
+    for k in range(40):
+        xp = f.step(_t(y[k])).cpu().numpy().astype(np.float64)
+        xo = o.step(y[k].astype(np.float32).astype(np.float64))
+        worst = max(worst, rel(xp, xo))
+    assert worst < 2e-2, worst
+    assert f.sync() == 0
+    f.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
 def test_step_matches_oracle_free_running(prec):
     """30 free-running frames from the cold start.  The per-analysis bound (1e-4, FP32) is
     checked above from identical states; here the transform's rounding (split-BF16 Newton-

@@ -25,8 +25,8 @@ def _built():
     _lib.load()
 
 
-def _kw(name, dense_noise=True):
-    w, g, doms, L, Ls = model(name)
+def _kw(name, dense_noise=True, m=None):
+    w, g, doms, L, Ls = model(name, m)
     kw = dict(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
               obstruction=w.obstruction, p0_sqrt=Ls, precision="mixed", path="fused", seed=w.seed,
               obs_block=w.obs_block)
@@ -37,8 +37,9 @@ def _kw(name, dense_noise=True):
     return kw
 
 
-# three systems of different sizes and ensemble sizes; one draws white process noise inline
-SYSTEMS = [("tiny-8x8", True), ("vlt-40x40", True), ("tiny-8x8", False)]
+# systems of different sizes and ensemble sizes (one of m >= 128, in the dual form); one draws
+# white process noise inline
+SYSTEMS = [("tiny-8x8", True, None), ("vlt-40x40", True, None), ("tiny-8x8", False, None), ("tiny-8x8", True, 150)]
 FRAMES = 12
 
 
@@ -47,8 +48,8 @@ def _frames(name):
     return np.ascontiguousarray(y[:FRAMES], dtype=np.float32)
 
 
-def _alone(name, dense, ys, bad_frame=None):
-    f = LETKF(**_kw(name, dense))
+def _alone(name, dense, m, ys, bad_frame=None):
+    f = LETKF(**_kw(name, dense, m))
     preds = []
     for k in range(len(ys)):
         y = ys[k].copy()
@@ -65,8 +66,8 @@ def _alone(name, dense, ys, bad_frame=None):
 def _serve(ys_list, pattern, bad=None):
     srv = Server(slots=2, max_pending=16)
     ids, outs = [], []
-    for name, dense in SYSTEMS:
-        sid = srv.admit(**_kw(name, dense))
+    for name, dense, m in SYSTEMS:
+        sid = srv.admit(**_kw(name, dense, m))
         ids.append(sid)
         outs.append(srv.set_output(sid, FRAMES))
     sent = [0] * len(SYSTEMS)
@@ -92,17 +93,17 @@ def _serve(ys_list, pattern, bad=None):
     return outs, [(x.cpu().numpy(), fr) for x, fr in states], info, recs
 
 
-PATTERN = [(1, 1, 1), (2, 0, 1), (0, 3, 0), (1, 1, 2), (3, 1, 0), (0, 0, 3), (2, 2, 2)]
+PATTERN = [(1, 1, 1, 1), (2, 0, 1, 0), (0, 3, 0, 2), (1, 1, 2, 1), (3, 1, 0, 0), (0, 0, 3, 3), (2, 2, 2, 2)]
 
 
 def test_batched_frames_equal_alone():
-    ys_list = [_frames(name) for name, _ in SYSTEMS]
+    ys_list = [_frames(name) for name, _, _ in SYSTEMS]
     outs, states, info, recs = _serve(ys_list, PATTERN)
     assert info["frames_done"] == FRAMES * len(SYSTEMS)
     assert info["batched_systems"] > info["batches"], "no batch held more than one system"
     assert max(r["batch_systems"] for r in recs) >= 2
-    for s, (name, dense) in enumerate(SYSTEMS):
-        preds, x, frame, st = _alone(name, dense, ys_list[s])
+    for s, (name, dense, m) in enumerate(SYSTEMS):
+        preds, x, frame, st = _alone(name, dense, m, ys_list[s])
         assert st == 0
         assert np.array_equal(outs[s], preds), (name, np.abs(outs[s] - preds).max())
         assert np.array_equal(states[s][0], x) and states[s][1] == frame == FRAMES
@@ -116,12 +117,12 @@ def test_batched_frames_equal_alone():
 
 
 def test_rejected_frame_inside_a_mix():
-    ys_list = [_frames(name) for name, _ in SYSTEMS]
+    ys_list = [_frames(name) for name, _, _ in SYSTEMS]
     outs, states, info, recs = _serve(ys_list, PATTERN, bad=(1, 4))
     bad = [r for r in recs if r["status"] != _lib.LETKF_OK]
     assert [(r["system"], r["frame"], r["status"]) for r in bad] == [(1, 4, _lib.LETKF_ENONFINITE)]
-    for s, (name, dense) in enumerate(SYSTEMS):
-        preds, x, frame, st = _alone(name, dense, ys_list[s], bad_frame=4 if s == 1 else None)
+    for s, (name, dense, m) in enumerate(SYSTEMS):
+        preds, x, frame, st = _alone(name, dense, m, ys_list[s], bad_frame=4 if s == 1 else None)
         assert st == (_lib.LETKF_ENONFINITE if s == 1 else 0)
         assert np.array_equal(outs[s], preds)
         assert np.array_equal(states[s][0], x)
@@ -150,6 +151,7 @@ def test_admission_by_footprint():
     ("vlt-40x40", dict(precision="fp32", path="plain")),
     ("vlt-40x40", dict(precision="mixed", path="fused")),
     ("tiny-8x8", dict(precision="fp32", path="fused", q_sqrt=None, q_white=0.1)),
+    ("tiny-8x8", dict(precision="mixed", path="fused", m=150)),
 ])
 def test_footprint_equals_allocated_bytes(cfg):
     name, over = cfg
@@ -161,9 +163,9 @@ def test_footprint_equals_allocated_bytes(cfg):
 
 
 def test_replay_runs_a_trace_in_real_time():
-    ys_list = [_frames(name) for name, _ in SYSTEMS]
+    ys_list = [_frames(name) for name, _, _ in SYSTEMS]
     srv = Server(slots=2, max_pending=32)
-    ids = [srv.admit(**_kw(name, dense)) for name, dense in SYSTEMS]
+    ids = [srv.admit(**_kw(name, dense, m)) for name, dense, m in SYSTEMS]
     sys_ids, t_ns, ys = [], [], []
     for k in range(FRAMES):
         for s in range(len(SYSTEMS)):
