@@ -216,3 +216,33 @@ class TruthStream:
             phi[i] = pa
             sig[i] = s
         return {"slopes": slopes, "phi_act": phi, "sigma": sig}
+
+
+def _compressed_chunk(args):
+    w, k0, k1, sub_valid, act_valid = args
+    fr = TruthStream(w).frames(k0, k1)
+    s = fr["slopes"]
+    y = np.concatenate([s[:, 0][:, sub_valid], s[:, 1][:, sub_valid]], axis=1).astype(np.float32)
+    return y, fr["phi_act"][:, act_valid].astype(np.float32), fr["sigma"]
+
+
+def compressed_frames(w: Workload, k0: int, k1: int, sub_valid: np.ndarray, act_valid: np.ndarray,
+                      workers: int = 1):
+    """Frames k0..k1-1 of TruthStream(w) on the given valid subapertures / actuators: slopes
+    (nf, p) FP32 (all x then all y), true actuator phase (nf, n_act) FP32 and the noise std
+    (nf,).  With workers > 1 the frames are made in chunks by spawned processes (each frame
+    depends only on its index, so the result is the same)."""
+    sub_valid = np.asarray(sub_valid, dtype=bool)
+    act_valid = np.asarray(act_valid, dtype=bool)
+    n = k1 - k0
+    if workers <= 1 or n < 64:
+        return _compressed_chunk((w, k0, k1, sub_valid, act_valid))
+    import concurrent.futures
+    import multiprocessing
+    edges = np.linspace(k0, k1, workers + 1).astype(int)
+    jobs = [(w, int(a), int(b), sub_valid, act_valid) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+    with concurrent.futures.ProcessPoolExecutor(max_workers=workers,
+                                                mp_context=multiprocessing.get_context("spawn")) as ex:
+        parts = list(ex.map(_compressed_chunk, jobs))
+    return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+            np.concatenate([p[2] for p in parts]))
