@@ -178,6 +178,16 @@ int letkf_get_state(letkf_ctx* ctx, void* x_dev, unsigned long long* frame);
  * phase.  With letkf_get_state this checkpoints and resumes a filter bit for bit. */
 int letkf_set_state(letkf_ctx* ctx, const void* x_dev, unsigned long long frame);
 
+/*
+ * letkf_set_graph: run letkf_step of a fused-path context as a CUDA graph launch (enable = 1) or
+ * as separate launches (0, the default).  Per frame parity the graph holds the
+ * fused kernel and, on a forked branch, the next frame's noise draw (normals kernel and GEMM);
+ * each call updates the kernel nodes' arguments (slopes, output, frame counter, ensemble
+ * buffers) and launches it on the context's stream.  Results are identical either way.
+ * Plain-path contexts: enable = 1 is LETKF_EINVAL, 0 is accepted.  Synchronises the stream.
+ */
+int letkf_set_graph(letkf_ctx* ctx, int enable);
+
 /* Wait for the context's queued work and return the first latched device error, clearing it. */
 int letkf_sync(letkf_ctx* ctx);
 

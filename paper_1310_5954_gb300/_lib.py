@@ -98,6 +98,7 @@ _SIGS = {
     "letkf_umma_selftest": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            _VP]),
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
     # letkf_serve.h
     "letkf_now_ns": (ctypes.c_longlong, []),
     "letkf_server_create": (ctypes.c_int, [ctypes.POINTER(letkf_server_params), ctypes.POINTER(ctypes.c_void_p)]),
@@ -220,6 +221,10 @@ def letkf_stage_name(stage: int) -> str:
 def letkf_umma_selftest(a_ptr: int, b_ptr: int, d_ptr: int, n: int, k: int, terms: int, b_layout: int = 0,
                         stream: int = 0) -> int:
     return load().letkf_umma_selftest(a_ptr, b_ptr, d_ptr, n, k, terms, b_layout, stream or None)
+
+
+def letkf_set_graph(ctx: int, enable: int) -> int:
+    return _check(load().letkf_set_graph(ctx, int(enable)), "letkf_set_graph")
 
 
 def letkf_footprint(params: letkf_params) -> int:

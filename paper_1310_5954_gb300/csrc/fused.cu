@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.hpp"
@@ -1442,6 +1444,11 @@ int fused_prepare(letkf_ctx* c) {
     }
     if (cudaMalloc(&c->Xi_side, xbytes) != cudaSuccess) return LETKF_ENOMEM;
     c->device_bytes += xbytes;
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return LETKF_ECUDA;
+    c->graph_on = 0;
     return LETKF_OK;
 }
 
@@ -1477,8 +1484,8 @@ int noise_prefetch(letkf_ctx* c, unsigned long long frame, cudaStream_t stream) 
     return LETKF_OK;
 }
 
-// Descriptor of system c's next frame; `stream` is the stream the kernel will run on.
-int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
+// Descriptor of system c's next frame, with the process-noise block V (dense noise) given.
+void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     letkf_ctx* c = f.c;
     if (f.sigma > 0) c->sigma = f.sigma;
     S->X = static_cast<const float*>(c->X[c->cur]);
@@ -1488,8 +1495,7 @@ int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
     S->vmode = 2;
     if (f.with_forecast) {
         if (c->Lq) {
-            const int rc = noise_ready(c, c->frame, stream, &S->V);
-            if (rc) return rc;
+            S->V = V;
             S->vmode = 0;
         } else if (c->q_white > 0) {
             S->vmode = 1;
@@ -1530,6 +1536,16 @@ int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
     S->sz_op = L.sz_op;
     S->sz_opg = L.sz_opg;
     S->sz_a = L.sz_a;
+}
+
+// Descriptor of system c's next frame; `stream` (the kernel's) waits for its noise block.
+int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
+    const float* V = nullptr;
+    if (f.with_forecast && f.c->Lq) {
+        const int rc = noise_ready(f.c, f.c->frame, stream, &V);
+        if (rc) return rc;
+    }
+    fill_desc(f, V, S);
     return LETKF_OK;
 }
 
@@ -1575,7 +1591,147 @@ int fused_batch(const FusedFrame* f, int n, int* queue, cudaStream_t stream) {
     return launch_batch(f, order.data(), n, queue, stream, f[0].c->sms);
 }
 
+void fused_graph_reset(letkf_ctx* c) {
+    for (int p = 0; p < 2; ++p) {
+        if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
+        if (c->graph[p]) cudaGraphDestroy(c->graph[p]);
+        c->gexec[p] = nullptr;
+        c->graph[p] = nullptr;
+        c->gnode_fused[p] = c->gnode_normals[p] = nullptr;
+    }
+}
+
+namespace {
+
+// Capture the step of frame parity p: the fused kernel (its parameters are replaced before every
+// launch) and, forked on the side stream, the draw of the next frame's noise into buffer p ^ 1.
+int graph_capture(letkf_ctx* c, int p) {
+    for (int q = 0; q < 2; ++q)
+        if (q == p) {
+            if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
+            if (c->graph[q]) cudaGraphDestroy(c->graph[q]);
+            c->gexec[q] = nullptr;
+            c->graph[q] = nullptr;
+        }
+    const bool dense = c->Lq != nullptr;
+    thread_local FusedBatch B;
+    FusedFrame f{c, nullptr, 0.0, nullptr, 1};
+    fill_desc(f, dense ? static_cast<const float*>(c->Vbuf[p]) : nullptr, &B.sys[0]);
+    B.sys[0].item0 = 0;
+    B.n_sys = 1;
+    B.n_items = c->n_dom;
+    B.queue = c->d_queue;
+    // captured on a stream of the context's own (the caller's may be the legacy default stream,
+    // which cannot be captured); the graph is launched on the caller's stream
+    cudaStream_t cs = c->cap_stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LETKF_ECUDA;
+    bool ok = true;
+    if (dense) {
+        ok = cudaEventRecord(c->ev_fork, cs) == cudaSuccess && cudaStreamWaitEvent(c->side, c->ev_fork, 0) == cudaSuccess;
+    }
+    if (ok) {
+        fused_kernel<<<std::min(c->sms, c->n_dom), FT, c->fused_smem, cs>>>(B);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    if (ok && dense) {
+        ok = draw_perturbations_on(c, c->frame + 1, c->Xi_side, c->Vbuf[p ^ 1], c->side, c->cublas_side) == LETKF_OK &&
+             cudaEventRecord(c->ev_join, c->side) == cudaSuccess &&
+             cudaStreamWaitEvent(cs, c->ev_join, 0) == cudaSuccess;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (!ok || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LETKF_ECUDA;
+    }
+    c->graph[p] = g;
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return LETKF_ECUDA;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return LETKF_ECUDA;
+    NormalsNode nn;
+    normals_node_params(c, 0, c->Xi_side, &nn);
+    c->gnode_fused[p] = c->gnode_normals[p] = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+        if (kp.func == reinterpret_cast<void*>(fused_kernel)) c->gnode_fused[p] = nd;
+        else if (kp.func == nn.params.func) c->gnode_normals[p] = nd;
+    }
+    if (!c->gnode_fused[p] || (dense && !c->gnode_normals[p])) return LETKF_ECUDA;
+    // the noise branch (normals and GEMM kernels) at the lowest priority, the frame's kernel at the
+    // highest: the branch fills SMs the fused kernel leaves idle rather than delaying its CTAs
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeAttrValue v;
+        std::memset(&v, 0, sizeof(v));
+        v.priority = nd == c->gnode_fused[p] ? greatest : least;
+        cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v);
+    }
+    cudaGetLastError();
+    if (cudaGraphInstantiate(&c->gexec[p], g, 0) != cudaSuccess) return LETKF_ECUDA;
+    return LETKF_OK;
+}
+
+// One frame (analysis + forecast) as a graph launch.
+int graph_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
+    const int p = (int)(c->frame & 1);
+    const bool dense = c->Lq != nullptr;
+    const float* V = nullptr;
+    int rc;
+    // this frame's noise: drawn by the previous graph launch on this stream, else drawn now
+    if (dense && (rc = noise_ready(c, c->frame, c->stream, &V))) return rc;
+    if (!c->gexec[p] && (rc = graph_capture(c, p))) {
+        fused_graph_reset(c);
+        return rc;
+    }
+    thread_local FusedBatch B;
+    FusedFrame f{c, y, sigma, xpred, 1};
+    fill_desc(f, V, &B.sys[0]);
+    B.sys[0].item0 = 0;
+    B.n_sys = 1;
+    B.n_items = c->n_dom;
+    B.queue = c->d_queue;
+    void* args[1] = {&B};
+    cudaKernelNodeParams kp;
+    kp.func = reinterpret_cast<void*>(fused_kernel);
+    kp.gridDim = dim3(std::min(c->sms, c->n_dom));
+    kp.blockDim = dim3(FT);
+    kp.sharedMemBytes = c->fused_smem;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (cudaGraphExecKernelNodeSetParams(c->gexec[p], c->gnode_fused[p], &kp) != cudaSuccess) return LETKF_ECUDA;
+    if (dense) {
+        NormalsNode nn;
+        normals_node_params(c, c->frame + 1, c->Xi_side, &nn);
+        if (cudaGraphExecKernelNodeSetParams(c->gexec[p], c->gnode_normals[p], &nn.params) != cudaSuccess)
+            return LETKF_ECUDA;
+    }
+    prof_begin(c, STAGE_FUSED);
+    const cudaError_t e = cudaGraphLaunch(c->gexec[p], c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return LETKF_ECUDA;
+    if (dense) {
+        // the launch read buffer p and drew frame + 1 into buffer p ^ 1 (stream-ordered events for
+        // steps that run outside a graph)
+        if (cudaEventRecord(c->ev_v_used[p], c->stream) != cudaSuccess ||
+            cudaEventRecord(c->ev_v_ready[p ^ 1], c->stream) != cudaSuccess)
+            return LETKF_ECUDA;
+        c->v_frame[p ^ 1] = c->frame + 1;
+    }
+    return LETKF_OK;
+}
+
+}  // namespace
+
 int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast) {
+    if (c->graph_on && with_forecast) return graph_step(c, y, sigma, xpred);
     FusedFrame f{c, y, sigma, xpred, with_forecast};
     prof_begin(c, STAGE_FUSED);
     const int rc = fused_batch(&f, 1, c->d_queue, c->stream);

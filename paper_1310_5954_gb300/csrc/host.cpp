@@ -196,6 +196,10 @@ void free_all(letkf_ctx* c) {
     }
     if (c->Xi_side) cudaFree(c->Xi_side);
     if (c->scratch) cudaFree(c->scratch);
+    letkf::fused_graph_reset(c);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
@@ -473,6 +477,16 @@ int letkf_sync(letkf_ctx* c) {
     if (st & letkf::ST_TIMEOUT) return LETKF_ETIMEOUT;
     if (st & letkf::ST_NONFINITE) return LETKF_ENONFINITE;
     if (st & letkf::ST_NOCONV) return LETKF_ENOCONV;
+    return LETKF_OK;
+}
+
+int letkf_set_graph(letkf_ctx* c, int enable) {
+    if (!c) return LETKF_EINVAL;
+    if (c->path != LETKF_PATH_FUSED) return enable ? LETKF_EINVAL : LETKF_OK;
+    CU(cudaSetDevice(c->device));
+    CU(cudaStreamSynchronize(c->stream));
+    letkf::fused_graph_reset(c);
+    c->graph_on = enable ? 1 : 0;
     return LETKF_OK;
 }
 

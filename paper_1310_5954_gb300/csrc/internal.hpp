@@ -96,6 +96,16 @@ struct letkf_ctx {
     void* Vbuf[2] = {nullptr, nullptr};
     void* Xi_side = nullptr;
     unsigned long long v_frame[2] = {~0ull, ~0ull};
+    // fused step as a CUDA graph (one per frame parity): the fused kernel and, on a forked branch,
+    // the next frame's noise draw; captured for the ensemble buffer in use (gcur)
+    int graph_on = 0;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphNode_t gnode_fused[2] = {nullptr, nullptr};
+    cudaGraphNode_t gnode_normals[2] = {nullptr, nullptr};
+    int gcur[2] = {-1, -1};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t cap_stream = nullptr;      // capture only
     // stage timing
     int prof_on = 0;
     std::vector<int> prof_stage;            // stage of each record
@@ -126,6 +136,16 @@ int draw_perturbations(letkf_ctx* c, unsigned long long frame);
 int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream,
                           cublasHandle_t handle);
 int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host);
+// Node parameters of the normals kernel draw_perturbations_on launches (arguments held in *nn).
+struct NormalsNode {
+    cudaKernelNodeParams params;
+    void* args[7];
+    void* out;
+    int ld, n_act, m;
+    unsigned long long seed;
+    uint32_t stream_id, frame;
+};
+int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
 int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
 
 // fused.cu
@@ -142,5 +162,6 @@ struct FusedFrame {
     int with_forecast;
 };
 int fused_batch(const FusedFrame* f, int n, int* queue, cudaStream_t stream);
+void fused_graph_reset(letkf_ctx* c);
 
 }  // namespace letkf

@@ -205,6 +205,36 @@ int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void
     return rc;
 }
 
+// Kernel-node parameters of the normals launch draw_perturbations_on makes for `frame` into xi
+// (same function, grid and arguments), for updating that node of a captured graph.
+int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn) {
+    const int gt = gemm_type_of(c);
+    const int nq = (c->n_act + 3) / 4;
+    nn->out = xi;
+    nn->ld = gt == 2 ? c->mb_pad : c->m_pad;
+    nn->n_act = c->n_act;
+    nn->m = c->m;
+    nn->seed = c->seed;
+    nn->stream_id = 1u;
+    nn->frame = (uint32_t)frame;
+    nn->args[0] = &nn->out;
+    nn->args[1] = &nn->ld;
+    nn->args[2] = &nn->n_act;
+    nn->args[3] = &nn->m;
+    nn->args[4] = &nn->seed;
+    nn->args[5] = &nn->stream_id;
+    nn->args[6] = &nn->frame;
+    cudaKernelNodeParams& kp = nn->params;
+    kp.func = gt == 0 ? (void*)normals_kernel<double>
+                      : (gt == 1 ? (void*)normals_kernel<float> : (void*)normals_kernel<__nv_bfloat16>);
+    kp.gridDim = dim3(grid_for((size_t)nq * c->m, 256));
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = nn->args;
+    kp.extra = nullptr;
+    return LETKF_OK;
+}
+
 int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis) {
     int vmode, vld;
     const void* Vp;

@@ -128,6 +128,10 @@ class LETKF:
         """Start (True) or stop (False) stage timing; stopping returns {stage: (ms, launches)}."""
         return _lib.letkf_profile(self.ctx, 1 if enable else 0)
 
+    def set_graph(self, enable: bool) -> None:
+        """Fused path: run each step as one CUDA graph launch, or as separate launches (default)."""
+        _lib.letkf_set_graph(self.ctx, 1 if enable else 0)
+
     def sync(self) -> int:
         return _lib.letkf_sync(self.ctx)
 

@@ -196,3 +196,34 @@ def test_fused_checkpoint_resume_is_bitwise():
         assert torch.equal(a.step(_t(y[k])), b.step(_t(y[k])))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("dense", [True, False])
+def test_graph_and_separate_launches_give_identical_frames(dense):
+    """letkf_step as a CUDA graph launch (the fused path's default) and as separate launches:
+    bit-identical predictions and states, also when switching between the two mid-run."""
+    from paper_1310_5954_gb300 import LETKF
+    y, _ = slopes("vlt-40x40", 12)
+    w, g, doms, L, Ls = model("vlt-40x40")
+    kw = dict(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
+              obstruction=w.obstruction, p0_sqrt=Ls, precision="mixed", path="fused", seed=w.seed)
+    if dense:
+        kw["q_sqrt"] = L
+    else:
+        kw["q_white"] = 0.05
+    a, b = LETKF(**kw), LETKF(**kw)
+    a.set_graph(True)
+    b.set_graph(False)
+    for k in range(12):
+        if k == 5:
+            a.set_graph(False)
+            b.set_graph(True)
+        if k == 8:
+            a.set_graph(True)
+        assert torch.equal(a.step(_t(y[k])), b.step(_t(y[k]))), k
+    xa, fa = a.get_state()
+    xb, fb = b.get_state()
+    assert torch.equal(xa, xb) and fa == fb == 12
+    assert a.sync() == 0 and b.sync() == 0
+    a.close()
+    b.close()
