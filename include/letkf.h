@@ -183,10 +183,13 @@ int letkf_set_state(letkf_ctx* ctx, const void* x_dev, unsigned long long frame)
  * as separate launches (0, the default).  Per frame parity the graph holds the
  * fused kernel and, on a forked branch, the next frame's noise draw (normals kernel and GEMM);
  * each call updates the kernel nodes' arguments (slopes, output, frame counter, ensemble
- * buffers) and launches it on the context's stream.  Results are identical either way.
+ * buffers) and launches it on the context's stream.  Results are identical either way.  If the
+ * step cannot be captured, the context goes back to separate launches (letkf_get_graph reads
+ * the current mode).
  * Plain-path contexts: enable = 1 is LETKF_EINVAL, 0 is accepted.  Synchronises the stream.
  */
 int letkf_set_graph(letkf_ctx* ctx, int enable);
+int letkf_get_graph(const letkf_ctx* ctx, int* enabled);
 
 /* Wait for the context's queued work and return the first latched device error, clearing it. */
 int letkf_sync(letkf_ctx* ctx);

@@ -99,6 +99,7 @@ _SIGS = {
                                            _VP]),
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
     "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     # letkf_serve.h
     "letkf_now_ns": (ctypes.c_longlong, []),
     "letkf_server_create": (ctypes.c_int, [ctypes.POINTER(letkf_server_params), ctypes.POINTER(ctypes.c_void_p)]),
@@ -225,6 +226,12 @@ def letkf_umma_selftest(a_ptr: int, b_ptr: int, d_ptr: int, n: int, k: int, term
 
 def letkf_set_graph(ctx: int, enable: int) -> int:
     return _check(load().letkf_set_graph(ctx, int(enable)), "letkf_set_graph")
+
+
+def letkf_get_graph(ctx: int) -> int:
+    v = ctypes.c_int()
+    _check(load().letkf_get_graph(ctx, ctypes.byref(v)), "letkf_get_graph")
+    return v.value
 
 
 def letkf_footprint(params: letkf_params) -> int:

@@ -812,6 +812,9 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
     tc_fence_after();
     const uint32_t tbase = ctl->tmem_base;
     uint32_t ph_load = 0, ph_mma = 0;
+    // a launch that follows this kernel through a programmatic edge may start now (it does not
+    // read what this kernel writes)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
     __syncthreads();
@@ -1435,7 +1438,8 @@ int fused_prepare(letkf_ctx* c) {
     if (cublasCreate(&c->cublas_side) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     if (cublasSetStream(c->cublas_side, c->side) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     const size_t vbytes = (size_t)c->n_act * c->m_pad * 4;
-    const size_t xbytes = std::max((size_t)c->n_act * c->mb_pad * 2, vbytes);
+    const size_t xbytes = c->precision == LETKF_PREC_MIXED ? noise_xi_bytes(c->n_act, c->m)
+                                                           : vbytes;
     for (int b = 0; b < 2; ++b) {
         if (cudaEventCreateWithFlags(&c->ev_v_ready[b], cudaEventDisableTiming) != cudaSuccess) return LETKF_ECUDA;
         if (cudaEventCreateWithFlags(&c->ev_v_used[b], cudaEventDisableTiming) != cudaSuccess) return LETKF_ECUDA;
@@ -1443,10 +1447,13 @@ int fused_prepare(letkf_ctx* c) {
         c->device_bytes += vbytes;
     }
     if (cudaMalloc(&c->Xi_side, xbytes) != cudaSuccess) return LETKF_ENOMEM;
+    if (cudaMemset(c->Xi_side, 0, xbytes) != cudaSuccess) return LETKF_ECUDA;   // tile padding stays zero
     c->device_bytes += xbytes;
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cublasCreate(&c->cublas_cap) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetStream(c->cublas_cap, c->cap_stream) != CUBLAS_STATUS_SUCCESS)
         return LETKF_ECUDA;
     c->graph_on = 0;
     return LETKF_OK;
@@ -1494,7 +1501,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->V = nullptr;
     S->vmode = 2;
     if (f.with_forecast) {
-        if (c->Lq) {
+        if (c->Lq || c->Lt) {
             S->V = V;
             S->vmode = 0;
         } else if (c->q_white > 0) {
@@ -1541,7 +1548,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
 // Descriptor of system c's next frame; `stream` (the kernel's) waits for its noise block.
 int make_desc(const FusedFrame& f, cudaStream_t stream, SysDesc* S) {
     const float* V = nullptr;
-    if (f.with_forecast && f.c->Lq) {
+    if (f.with_forecast && (f.c->Lq || f.c->Lt)) {
         const int rc = noise_ready(f.c, f.c->frame, stream, &V);
         if (rc) return rc;
     }
@@ -1567,7 +1574,7 @@ int launch_batch(const FusedFrame* f, const int* order, int n, int* queue, cudaS
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
     for (int k = 0; k < n; ++k) {
         letkf_ctx* c = f[order[k]].c;
-        if (f[order[k]].with_forecast && c->Lq) {
+        if (f[order[k]].with_forecast && (c->Lq || c->Lt)) {
             const int rc = noise_prefetch(c, c->frame, stream);
             if (rc) return rc;
         }
@@ -1603,6 +1610,8 @@ void fused_graph_reset(letkf_ctx* c) {
 
 namespace {
 
+constexpr int GRAPH_UNAVAILABLE = 1;
+
 // Capture the step of frame parity p: the fused kernel (its parameters are replaced before every
 // launch) and, forked on the side stream, the draw of the next frame's noise into buffer p ^ 1.
 int graph_capture(letkf_ctx* c, int p) {
@@ -1613,7 +1622,7 @@ int graph_capture(letkf_ctx* c, int p) {
             c->gexec[q] = nullptr;
             c->graph[q] = nullptr;
         }
-    const bool dense = c->Lq != nullptr;
+    const bool dense = c->Lq != nullptr || c->Lt != nullptr;
     thread_local FusedBatch B;
     FusedFrame f{c, nullptr, 0.0, nullptr, 1};
     fill_desc(f, dense ? static_cast<const float*>(c->Vbuf[p]) : nullptr, &B.sys[0]);
@@ -1623,20 +1632,29 @@ int graph_capture(letkf_ctx* c, int p) {
     B.queue = c->d_queue;
     // captured on a stream of the context's own (the caller's may be the legacy default stream,
     // which cannot be captured); the graph is launched on the caller's stream
+    // The noise branch hangs off the fused kernel by a programmatic edge: it is launched once every
+    // CTA of the fused kernel is resident (each signals at its start) instead of competing with
+    // them for SMs at launch, and it reads nothing the kernel writes.
     cudaStream_t cs = c->cap_stream;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LETKF_ECUDA;
-    bool ok = true;
-    if (dense) {
-        ok = cudaEventRecord(c->ev_fork, cs) == cudaSuccess && cudaStreamWaitEvent(c->side, c->ev_fork, 0) == cudaSuccess;
-    }
-    if (ok) {
-        fused_kernel<<<std::min(c->sms, c->n_dom), FT, c->fused_smem, cs>>>(B);
-        ok = cudaGetLastError() == cudaSuccess;
-    }
+    fused_kernel<<<std::min(c->sms, c->n_dom), FT, c->fused_smem, cs>>>(B);
+    bool ok = cudaGetLastError() == cudaSuccess;
     if (ok && dense) {
-        ok = draw_perturbations_on(c, c->frame + 1, c->Xi_side, c->Vbuf[p ^ 1], c->side, c->cublas_side) == LETKF_OK &&
-             cudaEventRecord(c->ev_join, c->side) == cudaSuccess &&
-             cudaStreamWaitEvent(cs, c->ev_join, 0) == cudaSuccess;
+        NormalsNode nn;
+        normals_node_params(c, c->frame + 1, c->Xi_side, &nn);
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr.val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = nn.params.gridDim;
+        cfg.blockDim = nn.params.blockDim;
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = cs;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        ok = cudaLaunchKernelExC(&cfg, nn.params.func, nn.params.kernelParams) == cudaSuccess &&
+             draw_product_on(c, c->Xi_side, c->Vbuf[p ^ 1], cs, c->cublas_cap) == LETKF_OK;
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
@@ -1682,14 +1700,14 @@ int graph_capture(letkf_ctx* c, int p) {
 // One frame (analysis + forecast) as a graph launch.
 int graph_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
     const int p = (int)(c->frame & 1);
-    const bool dense = c->Lq != nullptr;
+    const bool dense = c->Lq != nullptr || c->Lt != nullptr;
     const float* V = nullptr;
     int rc;
     // this frame's noise: drawn by the previous graph launch on this stream, else drawn now
     if (dense && (rc = noise_ready(c, c->frame, c->stream, &V))) return rc;
-    if (!c->gexec[p] && (rc = graph_capture(c, p))) {
+    if (!c->gexec[p] && graph_capture(c, p) != LETKF_OK) {
         fused_graph_reset(c);
-        return rc;
+        return GRAPH_UNAVAILABLE;
     }
     thread_local FusedBatch B;
     FusedFrame f{c, y, sigma, xpred, 1};
@@ -1731,7 +1749,12 @@ int graph_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
 }  // namespace
 
 int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast) {
-    if (c->graph_on && with_forecast) return graph_step(c, y, sigma, xpred);
+    if (c->graph_on && with_forecast) {
+        const int rc = graph_step(c, y, sigma, xpred);
+        if (rc != GRAPH_UNAVAILABLE) return rc;
+        c->graph_on = 0;   // this step cannot be captured here: separate launches from now on
+        cudaGetLastError();
+    }
     FusedFrame f{c, y, sigma, xpred, with_forecast};
     prof_begin(c, STAGE_FUSED);
     const int rc = fused_batch(&f, 1, c->d_queue, c->stream);

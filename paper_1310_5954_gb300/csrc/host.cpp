@@ -182,7 +182,7 @@ int alloc(letkf_ctx* c, void** p, size_t bytes) {
 }
 
 void free_all(letkf_ctx* c) {
-    void* ptrs[] = {c->X[0], c->X[1], c->Lq, c->Xi, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
+    void* ptrs[] = {c->X[0], c->X[1], c->Lq, c->Xi, c->Lt, c->noise_items, c->noise_tabs, c->noise_part, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
                     c->d_status, c->d_frame_bad, c->d_queue, c->tab.own_off, c->tab.own, c->tab.obs_off,
                     c->tab.obs_sub, c->tab.obs_corner, c->tab.halo_off, c->tab.halo, c->tab.order};
     for (void* p : ptrs)
@@ -199,6 +199,7 @@ void free_all(letkf_ctx* c) {
     letkf::fused_graph_reset(c);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->cublas_cap) cublasDestroy(c->cublas_cap);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
@@ -223,7 +224,6 @@ int validate(const letkf_params* p) {
 size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
     const size_t eb = p->precision == LETKF_PREC_FP64 ? 8 : 4;
     const size_t m_pad = eb == 8 ? (size_t)((p->m + 1) / 2) * 2 : (size_t)((p->m + 3) / 4) * 4;
-    const size_t mb_pad = (size_t)((p->m + 7) / 8) * 8;
     const size_t na = (size_t)h.n_act, n = 2 * na, nd = h.own_off.size() - 1;
     const size_t row = m_pad * eb;
     size_t b = 4 * (h.own_off.size() + h.own.size() + h.obs_off.size() + h.obs_sub.size() +
@@ -236,16 +236,19 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
         b += nd * p->m * row + nd * row + nd * p->m * row;
     } else {
         const size_t vbytes = na * m_pad * 4;
-        b += 2 * vbytes + std::max(na * mb_pad * 2, vbytes);
+        b += 2 * vbytes + (p->precision == LETKF_PREC_MIXED ? letkf::noise_xi_bytes(h.n_act, p->m)
+                                                             : vbytes);
         if (p->m + 1 > 128) {   // dual form: per-CTA halo anomalies
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) sms = 0;
             b += (size_t)sms * std::max(h.n_h_max, 1) * m_pad * 4;
         }
     }
-    if (p->q_sqrt) {
-        b += na * na * (p->precision == LETKF_PREC_MIXED ? 2 : eb);
-        b += p->precision == LETKF_PREC_MIXED ? na * mb_pad * 2 : na * row;
+    if (p->q_sqrt && p->precision == LETKF_PREC_MIXED) {
+        b += letkf::noise_plan(h.n_act, p->m, letkf::lower_triangular(p->q_sqrt, h.n_act)).bytes;
+        b += letkf::noise_xi_bytes(h.n_act, p->m);
+    } else if (p->q_sqrt) {
+        b += na * na * eb + na * row;
     }
     return b;
 }
@@ -258,7 +261,6 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     c->stream = (cudaStream_t)p->stream;
     const int eb = c->precision == LETKF_PREC_FP64 ? 8 : 4;
     c->m_pad = (eb == 8) ? ((c->m + 1) / 2) * 2 : ((c->m + 3) / 4) * 4;
-    c->mb_pad = ((c->m + 7) / 8) * 8;
     CU(cudaSetDevice(c->device));
     CU(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     build_model(c->host, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
@@ -487,6 +489,12 @@ int letkf_set_graph(letkf_ctx* c, int enable) {
     CU(cudaStreamSynchronize(c->stream));
     letkf::fused_graph_reset(c);
     c->graph_on = enable ? 1 : 0;
+    return LETKF_OK;
+}
+
+int letkf_get_graph(const letkf_ctx* c, int* enabled) {
+    if (!c || !enabled) return LETKF_EINVAL;
+    *enabled = c->graph_on;
     return LETKF_OK;
 }
 

@@ -49,7 +49,7 @@ struct HostModel {
 
 struct letkf_ctx {
     // parameters
-    int n_sub = 0, m = 0, m_pad = 0, mb_pad = 0, dom_sub = 0, halo = 0;
+    int n_sub = 0, m = 0, m_pad = 0, dom_sub = 0, halo = 0;
     int precision = 0, path = 0, obs_block = 1, device = 0;
     double a = 0, sigma = 0, q_white = 0;
     unsigned long long seed = 0;
@@ -65,8 +65,15 @@ struct letkf_ctx {
     int phase = 0;                  // 0: forecast phase, 1: analysis phase
     unsigned long long frame = 0;
     // process noise
-    void* Lq = nullptr;             // device L in the GEMM input type, n_act x n_act row-major
-    void* Xi = nullptr;             // normals, n_act x (mb_pad or m_pad)
+    void* Lq = nullptr;             // FP64 / FP32: device L, n_act x n_act row-major
+    void* Xi = nullptr;             // normals: n_act x m_pad (FP64 / FP32) or 64-row BF16 tiles (mixed)
+    // mixed precision: L as BF16 128 x 64 operand tiles (lower-triangle tiles only when L is lower
+    // triangular) and the work items of the noise kernel
+    void* Lt = nullptr;
+    int* noise_items = nullptr;     // int4 per item: row block, first tile, end tile, partial slot
+    int* noise_tabs = nullptr;      // per row block: first tile, items, first slot; split blocks
+    void* noise_part = nullptr;     // partial sums of row blocks split over several items
+    int noise_nb = 0, noise_np = 0, noise_tile_b = 0, noise_n_items = 0, noise_grid = 0, noise_n_rb = 0;
     void* V = nullptr;              // perturbations, n_act x m_pad (state type)
     cublasHandle_t cublas = nullptr;
     // scratch of the plain path
@@ -106,6 +113,7 @@ struct letkf_ctx {
     int gcur[2] = {-1, -1};
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t cap_stream = nullptr;      // capture only
+    cublasHandle_t cublas_cap = nullptr;
     // stage timing
     int prof_on = 0;
     std::vector<int> prof_stage;            // stage of each record
@@ -146,6 +154,23 @@ struct NormalsNode {
     uint32_t stream_id, frame;
 };
 int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
+
+// noise.cu: the mixed-precision draw V = L Xi on the tensor cores
+struct NoisePlan {
+    bool lower = false;
+    int nb = 0, nk = 0, np = 0, n_tiles = 0, n_items = 0, n_slots = 0;
+    size_t tile_b = 0, bytes = 0;    // bytes: device memory of the tiles, tables and partial sums
+    std::vector<int> prefix, jn, jslot, items;
+};
+bool lower_triangular(const double* L, int n);
+NoisePlan noise_plan(int n_act, int m, bool lower);
+size_t noise_xi_bytes(int n_act, int m);
+int noise_prepare(letkf_ctx* c, const double* L_host);
+int noise_draw(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream);
+// The product part of noise_draw / draw_perturbations_on (normals already in xi).
+int noise_product(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream);
+int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream, cublasHandle_t handle);
+int noise_normals_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
 int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
 
 // fused.cu

@@ -118,11 +118,6 @@ __global__ void f64_to_f32(const double* __restrict__ in, float* __restrict__ ou
         out[t] = (float)in[t];
 }
 
-__global__ void f64_to_bf16(const double* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-        out[t] = __float2bfloat16_rn((float)in[t]);
-}
-
 int grid_for(size_t work, int block) {
     size_t g = (work + block - 1) / block;
     if (g > 8192) g = 8192;
@@ -130,8 +125,8 @@ int grid_for(size_t work, int block) {
     return (int)g;
 }
 
-// V (n_act x m, ld m_pad) = L (n_act x n_act, row-major) * Xi (n_act x m, ld xld).
-// Column-major view used by cuBLAS: V^T = Xi^T L^T.
+// FP64 / FP32: V (n_act x m, ld m_pad) = L (n_act x n_act, row-major) * Xi (n_act x m, ld xld).
+// Column-major view used by cuBLAS: V^T = Xi^T L^T.  (Mixed precision uses noise.cu.)
 int noise_gemm(letkf_ctx* c, const void* L, const void* Xi, int xld, int gemm_type, void* V) {
     const int m = c->m, na = c->n_act;
     cublasStatus_t st;
@@ -144,10 +139,7 @@ int noise_gemm(letkf_ctx* c, const void* L, const void* Xi, int xld, int gemm_ty
         st = cublasSgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, (const float*)Xi, xld,
                          (const float*)L, na, &zero, (float*)V, c->m_pad);
     } else {
-        const float one = 1.f, zero = 0.f;
-        st = cublasGemmEx(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, Xi, CUDA_R_16BF, xld, L,
-                          CUDA_R_16BF, na, &zero, V, CUDA_R_32F, c->m_pad, CUBLAS_COMPUTE_32F,
-                          CUBLAS_GEMM_DEFAULT);
+        return LETKF_EINVAL;
     }
     return st == CUBLAS_STATUS_SUCCESS ? LETKF_OK : LETKF_ECUDA;
 }
@@ -185,22 +177,29 @@ int draw_perturbations_impl(letkf_ctx* c, unsigned long long frame) {
 
 int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream,
                           cublasHandle_t handle) {
+    if (c->Lt) return noise_draw(c, frame, xi, v_out, stream);
     const int gt = gemm_type_of(c);
     const int nq = (c->n_act + 3) / 4;
     const int g = grid_for((size_t)nq * c->m, 256);
     if (gt == 0)
         normals_kernel<double><<<g, 256, 0, stream>>>((double*)xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
                                                       (uint32_t)frame);
-    else if (gt == 1)
+    else
         normals_kernel<float><<<g, 256, 0, stream>>>((float*)xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
                                                      (uint32_t)frame);
-    else
-        normals_kernel<__nv_bfloat16><<<g, 256, 0, stream>>>((__nv_bfloat16*)xi, c->mb_pad, c->n_act, c->m,
-                                                             c->seed, 1u, (uint32_t)frame);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
     cublasHandle_t saved = c->cublas;
     c->cublas = handle;
-    const int rc = noise_gemm(c, c->Lq, xi, gt == 2 ? c->mb_pad : c->m_pad, gt, v_out);
+    const int rc = noise_gemm(c, c->Lq, xi, c->m_pad, gt, v_out);
+    c->cublas = saved;
+    return rc;
+}
+
+int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream, cublasHandle_t handle) {
+    if (c->Lt) return noise_product(c, xi, v_out, stream);
+    cublasHandle_t saved = c->cublas;
+    c->cublas = handle;
+    const int rc = noise_gemm(c, c->Lq, xi, c->m_pad, gemm_type_of(c), v_out);
     c->cublas = saved;
     return rc;
 }
@@ -208,10 +207,11 @@ int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void
 // Kernel-node parameters of the normals launch draw_perturbations_on makes for `frame` into xi
 // (same function, grid and arguments), for updating that node of a captured graph.
 int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn) {
+    if (c->Lt) return noise_normals_params(c, frame, xi, nn);
     const int gt = gemm_type_of(c);
     const int nq = (c->n_act + 3) / 4;
     nn->out = xi;
-    nn->ld = gt == 2 ? c->mb_pad : c->m_pad;
+    nn->ld = c->m_pad;
     nn->n_act = c->n_act;
     nn->m = c->m;
     nn->seed = c->seed;
@@ -225,8 +225,7 @@ int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, Normal
     nn->args[5] = &nn->stream_id;
     nn->args[6] = &nn->frame;
     cudaKernelNodeParams& kp = nn->params;
-    kp.func = gt == 0 ? (void*)normals_kernel<double>
-                      : (gt == 1 ? (void*)normals_kernel<float> : (void*)normals_kernel<__nv_bfloat16>);
+    kp.func = gt == 0 ? (void*)normals_kernel<double> : (void*)normals_kernel<float>;
     kp.gridDim = dim3(grid_for((size_t)nq * c->m, 256));
     kp.blockDim = dim3(256);
     kp.sharedMemBytes = 0;
@@ -242,7 +241,7 @@ int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analys
         vmode = 0;
         Vp = v_user;
         vld = c->m;
-    } else if (c->Lq) {
+    } else if (c->Lq || c->Lt) {
         int rc = draw_perturbations(c, c->frame);
         if (rc) return rc;
         vmode = 0;
@@ -278,23 +277,28 @@ int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
     const size_t nn = (size_t)na * na;
     const size_t row = (size_t)c->m_pad * eb;
     // buffers for the process-noise draws of later frames
-    if (L_host) {
+    if (L_host && c->precision == LETKF_PREC_MIXED) {
+        const int rc = noise_prepare(c, L_host);
+        if (rc) return rc;
+        const size_t xib = noise_xi_bytes(na, m);
+        if (cudaMalloc(&c->Xi, xib) != cudaSuccess) return LETKF_ENOMEM;
+        cudaMemset(c->Xi, 0, xib);
+        c->device_bytes += xib;
+    } else if (L_host) {
         void* tmp = nullptr;
         if (cudaMalloc(&tmp, nn * 8) != cudaSuccess) return LETKF_ENOMEM;
         cudaMemcpy(tmp, L_host, nn * 8, cudaMemcpyHostToDevice);
-        const size_t lbytes = c->precision == LETKF_PREC_MIXED ? nn * 2 : nn * eb;
+        const size_t lbytes = nn * eb;
         if (cudaMalloc(&c->Lq, lbytes) != cudaSuccess) { cudaFree(tmp); return LETKF_ENOMEM; }
         c->device_bytes += lbytes;
         const int g = grid_for(nn, 256);
         if (f64)
             cudaMemcpyAsync(c->Lq, tmp, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
-        else if (c->precision == LETKF_PREC_FP32)
-            f64_to_f32<<<g, 256, 0, c->stream>>>((const double*)tmp, (float*)c->Lq, nn);
         else
-            f64_to_bf16<<<g, 256, 0, c->stream>>>((const double*)tmp, (__nv_bfloat16*)c->Lq, nn);
+            f64_to_f32<<<g, 256, 0, c->stream>>>((const double*)tmp, (float*)c->Lq, nn);
         cudaStreamSynchronize(c->stream);
         cudaFree(tmp);
-        const size_t xib = c->precision == LETKF_PREC_MIXED ? (size_t)na * c->mb_pad * 2 : (size_t)na * row;
+        const size_t xib = (size_t)na * row;
         if (cudaMalloc(&c->Xi, xib) != cudaSuccess) return LETKF_ENOMEM;
         cudaMemset(c->Xi, 0, xib);
         c->device_bytes += xib;

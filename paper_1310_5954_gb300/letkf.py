@@ -132,6 +132,10 @@ class LETKF:
         """Fused path: run each step as one CUDA graph launch, or as separate launches (default)."""
         _lib.letkf_set_graph(self.ctx, 1 if enable else 0)
 
+    def graph(self) -> bool:
+        """Whether steps currently run as CUDA graph launches."""
+        return bool(_lib.letkf_get_graph(self.ctx))
+
     def sync(self) -> int:
         return _lib.letkf_sync(self.ctx)
 

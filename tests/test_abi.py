@@ -70,14 +70,20 @@ def test_footprint_on_the_host(lib):
     base = dict(n_sub=8, m=20, ar1_a=0.99, sigma=0.1, dom_sub=4, halo=1, precision="mixed", path="fused")
     f0 = footprint(**base, q_white=0.1)
     n_act = 69                                  # 8x8 circular pupil (oracle geometry pins)
-    L = np.eye(n_act)
-    f1 = footprint(**base, q_sqrt=L)
-    # a dense noise factor adds the BF16 factor and the BF16 normals (rows of m rounded up to 8)
-    assert f1 - f0 == n_act * n_act * 2 + n_act * 24 * 2
-    # per member: the two ensemble buffers (2 x 2 n_act rows), the perturbation buffer (n_act)
-    # and the fused path's two noise buffers and normals (3 x n_act), FP32
+    f1 = footprint(**base, q_sqrt=np.eye(n_act))
+    # a dense noise factor adds its BF16 tiles (one 128-row block x two 64-column tiles), one work
+    # item (16 B), the block's table (4 ints) and the normals' tiles (2 x 64 rows x 32 columns, BF16)
+    assert f1 - f0 == 2 * 128 * 64 * 2 + 16 + 16 + 2 * 64 * 32 * 2
+    # only the tiles touching the lower triangle are kept for a lower-triangular factor: 16x16 has
+    # 241 actuators, two row blocks of four column tiles, and 2 + 4 tiles of the eight
+    b16 = dict(base, n_sub=16)
+    rng = np.random.default_rng(0)
+    full = rng.standard_normal((241, 241))
+    assert footprint(**b16, q_sqrt=full) - footprint(**b16, q_sqrt=np.tril(full)) == 2 * 128 * 64 * 2
+    # per member: the two ensemble buffers (2 x 2 n_act rows), the perturbation buffer and the
+    # fused path's two noise buffers (3 x n_act), FP32; the BF16 normals tile widens from 32 to 48
     f2 = footprint(**dict(base, m=40), q_white=0.1)
-    assert f2 - f0 == (4 + 1 + 3) * n_act * 20 * 4
+    assert f2 - f0 == (4 + 1 + 2) * n_act * 20 * 4 + 128 * (48 - 32) * 2
     with pytest.raises(_lib.LETKFError):
         footprint(**dict(base, m=1))
 

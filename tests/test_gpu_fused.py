@@ -214,7 +214,10 @@ def test_graph_and_separate_launches_give_identical_frames(dense):
     a, b = LETKF(**kw), LETKF(**kw)
     a.set_graph(True)
     b.set_graph(False)
-    for k in range(12):
+    a.step(_t(y[0]))
+    assert a.graph(), "the step could not be captured"
+    b.step(_t(y[0]))
+    for k in range(1, 12):
         if k == 5:
             a.set_graph(False)
             b.set_graph(True)
@@ -227,3 +230,26 @@ def test_graph_and_separate_launches_give_identical_frames(dense):
     assert a.sync() == 0 and b.sync() == 0
     a.close()
     b.close()
+
+
+def test_mixed_noise_draw_matches_oracle_and_repeats():
+    """Mixed precision draws v = L xi with the BF16 tensor-core kernel over the stored lower-
+    triangle tiles of L: the relative L2 error against the FP64 draw is at the BF16 level
+    (operands rounded to 8 significant bits), and drawing a frame twice gives the same bits."""
+    w, g, doms, L, Ls = model("vlt-40x40")
+    f = gpu_filter("vlt-40x40", "mixed", "fused")
+    o = oracle_filter("vlt-40x40")
+    zero = torch.zeros((f.info.n, f.info.m), dtype=torch.float32, device="cuda")
+    draws = []
+    for frame in (3, 4, 3):
+        f.set_state(zero, frame)
+        f.forecast()
+        x, fr = f.get_state()
+        assert fr == frame + 1
+        v = x[: g.n_act].cpu().numpy().astype(np.float64)
+        assert rel(v, o.perturbation(frame)) < 5e-3, (frame, rel(v, o.perturbation(frame)))
+        assert not x[g.n_act:].any()
+        draws.append(v)
+    assert np.array_equal(draws[0], draws[2]) and not np.array_equal(draws[0], draws[1])
+    assert f.sync() == 0
+    f.close()
