@@ -1033,20 +1033,31 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             ph_mma ^= 1;
             tc_fence_after();
             float r2 = 0.f;
+            {   // the next chunk's TMEM load is in flight while this one is processed
+                uint32_t rc[8], rn[8];
+                tmem_ld8_async(tl + TM_P, rc);
+                tmem_wait_ld(rc);
 #pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float pv[8], tv[8];
-                tmem_ld8(tl + TM_P + 8 * q8, pv);
+                for (int q8 = 0; q8 < nq; ++q8) {
+                    if (q8 + 1 < nq) tmem_ld8_async(tl + TM_P + 8 * (q8 + 1), rn);
+                    float tv[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = col0 + 8 * q8 + u;
-                    const bool in = row < m && j < m;
-                    const float id = (row == j) ? 1.f : 0.f;
-                    const float rr = id - pv[u];
-                    if (in) r2 += rr * rr;
-                    tv[u] = in ? 1.5f * id - 0.5f * pv[u] : 0.f;
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = col0 + 8 * q8 + u;
+                        const bool in = row < m && j < m;
+                        const float id = (row == j) ? 1.f : 0.f;
+                        const float pv = __uint_as_float(rc[u]);
+                        const float rr = id - pv;
+                        if (in) r2 += rr * rr;
+                        tv[u] = in ? 1.5f * id - 0.5f * pv : 0.f;
+                    }
+                    if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
+                    if (q8 + 1 < nq) {
+                        tmem_wait_ld(rn);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) rc[u] = rn[u];
+                    }
                 }
-                if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
             }
             r2 = block_sum(ctl, r2);
             const float rn = sqrtf(r2);
@@ -1067,9 +1078,16 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             tc_fence_after();
 #pragma unroll 1
             for (int q8 = 0; q8 < nq; ++q8) {
+                uint32_t ry[8], rz[8];
+                tmem_ld8_async(tl + TM_Y + 8 * q8, ry);
+                tmem_ld8_async(tl + TM_Z + 8 * q8, rz);
+                tmem_wait_ld(ry, rz);
                 float yv[8], zv[8];
-                tmem_ld8(tl + TM_Y + 8 * q8, yv);
-                tmem_ld8(tl + TM_Z + 8 * q8, zv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    yv[u] = __uint_as_float(ry[u]);
+                    zv[u] = __uint_as_float(rz[u]);
+                }
                 if (row < NP) {
                     store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
                     store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);

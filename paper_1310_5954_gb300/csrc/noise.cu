@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(NT) noise_kernel(const __grid_constant__ Noise
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (q0 + u < (a.np >> 3)) tmem_ld8_async(tl + 8 * (q0 + u), r[u]);
-            tmem_wait_ld();
+            tmem_wait_ld(r[0], r[1]);
+            tmem_wait_ld(r[2], r[3]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int q8 = q0 + u;
