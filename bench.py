@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=30)
     ap.add_argument("--no-serving", action="store_true", help="skip the two serving-loop legs")
     ap.add_argument("--graph", action="store_true", help="fused path: each step as one CUDA graph launch")
+    ap.add_argument("--no-autotune", action="store_true", help="fused path: default launch tuning")
     ap.add_argument("--mix-seconds", type=float, default=2.0, help="arrival window of the serving mix")
     ap.add_argument("--ns-frames", type=int, default=10000, help="frames of the non-stationary serving run")
     return ap.parse_args()
@@ -482,9 +483,12 @@ def main():
 
     def timed(path, prec, seed_offset):
         f = make_filter(w, path, prec, L, Ls, seed_offset)
-        if path == "fused":
-            f.set_graph(args.graph)
         ydev = torch.as_tensor(y, dtype=f.dtype, device=dev).contiguous()
+        if path == "fused":
+            if args.graph:
+                f.set_graph(True)
+            elif not args.no_autotune:
+                tuned[path] = f.autotune(ydev[0], frames=20)
         if world > 1:
             dist.barrier()
         ms, preds, wall = run_device(f, ydev, K, W, flush, torch)
@@ -492,6 +496,7 @@ def main():
         status = f.sync()
         return f, ms, preds, wall, prof, ydev, status
 
+    tuned = {}
     clocks = Clocks(local)
     f, ms, preds, wall, prof, ydev, status = timed(args.path, precision, rank)
     clk = clocks.stop()
@@ -507,7 +512,10 @@ def main():
     y_host = torch.as_tensor(y, dtype=f.dtype).pin_memory()
     fe = make_filter(w, args.path, precision, L, Ls, rank)
     if args.path == "fused":
-        fe.set_graph(args.graph)
+        if args.graph:
+            fe.set_graph(True)
+        elif args.path in tuned:
+            fe.set_tuning(**tuned[args.path]["tuning"])
     e2e_fps, e2e_lat, h2d, d2h = run_e2e(fe, y_host, K, W, torch)
     fe.close()
     burn = min(50, (W + K) // 4)
@@ -520,7 +528,9 @@ def main():
                                f"obstruction, m={w.m}, {f.info.n_domains} domains {w.dom_sub}x{w.dom_sub}+halo "
                                f"{w.halo}, n={f.info.n}, p={f.info.p}",
                    "path": args.path, "precision": precision,
-                   "cuda_graph": args.path == "fused" and args.graph,
+                   "cuda_graph": args.path == "fused" and (args.graph or
+                                                            bool(tuned.get(args.path, {}).get("tuning", {}).get("graph"))),
+                   "launch_tuning": tuned.get(args.path),
                    "l2": f"flushed before every timed step ({args.flush_mb} MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),

@@ -191,6 +191,25 @@ int letkf_set_state(letkf_ctx* ctx, const void* x_dev, unsigned long long frame)
 int letkf_set_graph(letkf_ctx* ctx, int enable);
 int letkf_get_graph(const letkf_ctx* ctx, int* enabled);
 
+/*
+ * Launch tuning of the fused path (the paper has no counterpart).  Neither knob changes any
+ * result: fused_grid is the number of CTAs of the fused kernel for this context (0: one per SM,
+ * capped at the number of domains; at most the SM count), graph is letkf_set_graph's mode.
+ * letkf_autotune times `frames` letkf_step calls with the slopes y_dev (p elements) for each
+ * candidate (one CTA per SM, or the fewest CTAs taking the same number of rounds of domains;
+ * graph off or on), keeps the fastest and reports it and its milliseconds per frame (either
+ * pointer may be NULL).  The context's ensemble, frame counter, noise std and latched status
+ * are restored afterwards.  Plain-path contexts: tuning is fixed at {0, 0}.
+ */
+typedef struct letkf_tuning {
+    int fused_grid;
+    int graph;
+} letkf_tuning;
+
+int letkf_get_tuning(const letkf_ctx* ctx, letkf_tuning* out);
+int letkf_set_tuning(letkf_ctx* ctx, const letkf_tuning* tuning);
+int letkf_autotune(letkf_ctx* ctx, const void* y_dev, int frames, letkf_tuning* best, double* ms_per_frame);
+
 /* Wait for the context's queued work and return the first latched device error, clearing it. */
 int letkf_sync(letkf_ctx* ctx);
 

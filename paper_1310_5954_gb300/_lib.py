@@ -72,6 +72,10 @@ class letkf_server_info(ctypes.Structure):
                 ("batched_systems", ctypes.c_ulonglong)]
 
 
+class letkf_tuning(ctypes.Structure):
+    _fields_ = [("fused_grid", ctypes.c_int), ("graph", ctypes.c_int)]
+
+
 N_STAGES = 8
 
 
@@ -100,6 +104,10 @@ _SIGS = {
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
     "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "letkf_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
+    "letkf_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
+    "letkf_autotune": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(letkf_tuning),
+                                      ctypes.POINTER(ctypes.c_double)]),
     # letkf_serve.h
     "letkf_now_ns": (ctypes.c_longlong, []),
     "letkf_server_create": (ctypes.c_int, [ctypes.POINTER(letkf_server_params), ctypes.POINTER(ctypes.c_void_p)]),
@@ -232,6 +240,25 @@ def letkf_get_graph(ctx: int) -> int:
     v = ctypes.c_int()
     _check(load().letkf_get_graph(ctx, ctypes.byref(v)), "letkf_get_graph")
     return v.value
+
+
+def letkf_get_tuning(ctx: int) -> dict:
+    t = letkf_tuning()
+    _check(load().letkf_get_tuning(ctx, ctypes.byref(t)), "letkf_get_tuning")
+    return {"fused_grid": t.fused_grid, "graph": t.graph}
+
+
+def letkf_set_tuning(ctx: int, fused_grid: int, graph: int) -> int:
+    t = letkf_tuning(int(fused_grid), int(graph))
+    return _check(load().letkf_set_tuning(ctx, ctypes.byref(t)), "letkf_set_tuning")
+
+
+def letkf_autotune(ctx: int, y_ptr: int, frames: int = 20):
+    """Returns ({'fused_grid', 'graph'}, ms per frame of the best candidate)."""
+    t = letkf_tuning()
+    ms = ctypes.c_double()
+    _check(load().letkf_autotune(ctx, y_ptr, int(frames), ctypes.byref(t), ctypes.byref(ms)), "letkf_autotune")
+    return {"fused_grid": t.fused_grid, "graph": t.graph}, ms.value
 
 
 def letkf_footprint(params: letkf_params) -> int:

@@ -1588,7 +1588,9 @@ int launch_batch(const FusedFrame* f, const int* order, int n, int* queue, cudaS
     B.n_sys = n;
     B.n_items = items;
     B.queue = queue;
-    fused_kernel<<<std::min(sms, items), FT, smem, stream>>>(B);
+    // one system alone runs on its tuned grid (letkf_set_tuning); a batch fills every SM
+    const int grid = n == 1 && f[order[0]].c->fused_grid > 0 ? f[order[0]].c->fused_grid : sms;
+    fused_kernel<<<std::min(grid, items), FT, smem, stream>>>(B);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
     for (int k = 0; k < n; ++k) {
         letkf_ctx* c = f[order[k]].c;
@@ -1655,7 +1657,7 @@ int graph_capture(letkf_ctx* c, int p) {
     // them for SMs at launch, and it reads nothing the kernel writes.
     cudaStream_t cs = c->cap_stream;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LETKF_ECUDA;
-    fused_kernel<<<std::min(c->sms, c->n_dom), FT, c->fused_smem, cs>>>(B);
+    fused_kernel<<<std::min(c->fused_grid > 0 ? c->fused_grid : c->sms, c->n_dom), FT, c->fused_smem, cs>>>(B);
     bool ok = cudaGetLastError() == cudaSuccess;
     if (ok && dense) {
         NormalsNode nn;
@@ -1737,7 +1739,7 @@ int graph_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
     void* args[1] = {&B};
     cudaKernelNodeParams kp;
     kp.func = reinterpret_cast<void*>(fused_kernel);
-    kp.gridDim = dim3(std::min(c->sms, c->n_dom));
+    kp.gridDim = dim3(std::min(c->fused_grid > 0 ? c->fused_grid : c->sms, c->n_dom));
     kp.blockDim = dim3(FT);
     kp.sharedMemBytes = c->fused_smem;
     kp.kernelParams = args;

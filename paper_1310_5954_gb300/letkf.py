@@ -8,6 +8,8 @@ current torch stream.
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 from typing import Optional
 
 import numpy as np
@@ -83,6 +85,7 @@ class LETKF:
             self.ctx = _lib.letkf_create(p)
         self._keep = []
         self.info = _lib.letkf_get_info(self.ctx)
+        self.noise_kind = "dense" if q_sqrt is not None else ("white" if q_white > 0 else "none")
         self.dtype = torch.float64 if self.info.state_bytes == 8 else torch.float32
         self.precision, self.path = precision, path
 
@@ -131,6 +134,43 @@ class LETKF:
     def set_graph(self, enable: bool) -> None:
         """Fused path: run each step as one CUDA graph launch, or as separate launches (default)."""
         _lib.letkf_set_graph(self.ctx, 1 if enable else 0)
+
+    def tuning(self) -> dict:
+        return _lib.letkf_get_tuning(self.ctx)
+
+    def set_tuning(self, fused_grid: int = 0, graph: int = 0) -> None:
+        _lib.letkf_set_tuning(self.ctx, fused_grid, graph)
+
+    def tuning_key(self) -> str:
+        """What the launch tuning depends on: geometry, domains, ensemble, path and the GPU."""
+        import torch
+        i = self.info
+        props = torch.cuda.get_device_properties(self.device)
+        return (f"n_sub={i.n_sub} n_act={i.n_act} n_subv={i.n_subv} domains={i.n_domains} m={i.m} "
+                f"precision={self.precision} path={self.path} noise={self.noise_kind} "
+                f"gpu={props.name} sms={props.multi_processor_count}")
+
+    def autotune(self, y, frames: int = 20, cache: Optional[str] = None) -> dict:
+        """Pick the fastest launch tuning for this system (letkf_autotune) and apply it.  With a
+        cache path (JSON), a stored result for the same tuning_key() is applied without trials
+        and new results are added to the file."""
+        key = self.tuning_key()
+        data = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                data = json.load(fh)
+            if key in data:
+                self.set_tuning(**data[key]["tuning"])
+                return data[key]
+        tuning, ms = _lib.letkf_autotune(self.ctx, self._dev(y, self.info.p, "y"), frames)
+        rec = {"tuning": tuning, "ms_per_frame": ms, "frames": int(frames)}
+        if cache:
+            data[key] = rec
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(data, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return rec
 
     def graph(self) -> bool:
         """Whether steps currently run as CUDA graph launches."""

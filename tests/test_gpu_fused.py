@@ -253,3 +253,31 @@ def test_mixed_noise_draw_matches_oracle_and_repeats():
     assert np.array_equal(draws[0], draws[2]) and not np.array_equal(draws[0], draws[1])
     assert f.sync() == 0
     f.close()
+
+
+def test_autotune_restores_the_filter_and_changes_no_result(tmp_path):
+    """letkf_autotune tries launch configurations on trial frames: afterwards the ensemble and
+    frame counter are those from before, and the tuned filter's frames equal an untuned twin's
+    bit for bit.  A second context with the same key takes the cached result without trials."""
+    y, _ = slopes("vlt-40x40", 8)
+    a = gpu_filter("vlt-40x40", "mixed", "fused")
+    b = gpu_filter("vlt-40x40", "mixed", "fused")
+    for k in range(2):
+        assert torch.equal(a.step(_t(y[k])), b.step(_t(y[k])))
+    x0, f0 = a.get_state()
+    x0 = x0.clone()
+    cache = str(tmp_path / "tuning.json")
+    rec = a.autotune(_t(y[2]), frames=4, cache=cache)
+    x1, f1 = a.get_state()
+    assert torch.equal(x0, x1) and f1 == f0 == 2
+    assert a.sync() == 0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert rec["tuning"]["graph"] in (0, 1) and 1 <= rec["tuning"]["fused_grid"] <= sms
+    assert a.tuning() == rec["tuning"] and rec["ms_per_frame"] > 0
+    for k in range(2, 8):
+        assert torch.equal(a.step(_t(y[k])), b.step(_t(y[k]))), k
+    c = gpu_filter("vlt-40x40", "mixed", "fused")
+    assert c.autotune(_t(y[0]), cache=cache) == rec and c.tuning() == rec["tuning"]
+    for f in (a, b, c):
+        assert f.sync() == 0
+        f.close()
