@@ -135,6 +135,23 @@ int letkf_create(const letkf_params* params, letkf_ctx** out);
  */
 int letkf_footprint(const letkf_params* params, unsigned long long* bytes);
 
+/*
+ * letkf_domain_tables: the geometry and domain decomposition letkf_create would build for these
+ * parameters (Sect. 2.3; host only, no GPU).  sizes is filled first; every array may be NULL and
+ * otherwise holds: own_off[n_dom + 1] / own[own_total] the valid actuators each domain updates
+ * (both instants), obs_off[n_dom + 1] / obs_sub[obs_total] its observed valid subapertures,
+ * halo_off[n_dom + 1] / halo[halo_total] the valid actuators at the corners of those
+ * subapertures (the rows of the observed instant its analysis reads), block[n_dom] its block
+ * index I * blocks_per_side + J.  Indices are valid-actuator / valid-subaperture numbers.
+ */
+typedef struct letkf_domain_sizes {
+    int n_sub, n_act, n_subv, n_dom, blocks_per_side;
+    int own_total, obs_total, halo_total;
+} letkf_domain_sizes;
+
+int letkf_domain_tables(const letkf_params* params, letkf_domain_sizes* sizes, int* own_off, int* own,
+                        int* obs_off, int* obs_sub, int* halo_off, int* halo, int* block);
+
 /* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
 int letkf_destroy(letkf_ctx* ctx);
 

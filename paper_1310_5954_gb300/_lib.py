@@ -72,6 +72,12 @@ class letkf_server_info(ctypes.Structure):
                 ("batched_systems", ctypes.c_ulonglong)]
 
 
+class letkf_domain_sizes(ctypes.Structure):
+    _fields_ = [("n_sub", ctypes.c_int), ("n_act", ctypes.c_int), ("n_subv", ctypes.c_int), ("n_dom", ctypes.c_int),
+                ("blocks_per_side", ctypes.c_int), ("own_total", ctypes.c_int), ("obs_total", ctypes.c_int),
+                ("halo_total", ctypes.c_int)]
+
+
 class letkf_tuning(ctypes.Structure):
     _fields_ = [("fused_grid", ctypes.c_int), ("graph", ctypes.c_int)]
 
@@ -103,6 +109,8 @@ _SIGS = {
                                            _VP]),
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
     "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "letkf_domain_tables": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(letkf_domain_sizes),
+                                           _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
     "letkf_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
@@ -259,6 +267,24 @@ def letkf_autotune(ctx: int, y_ptr: int, frames: int = 20):
     ms = ctypes.c_double()
     _check(load().letkf_autotune(ctx, y_ptr, int(frames), ctypes.byref(t), ctypes.byref(ms)), "letkf_autotune")
     return {"fused_grid": t.fused_grid, "graph": t.graph}, ms.value
+
+
+def letkf_domain_tables(params: letkf_params) -> dict:
+    """Host-side geometry and domains (numpy int32 arrays) of letkf_domain_tables."""
+    import numpy as np
+    sz = letkf_domain_sizes()
+    _check(load().letkf_domain_tables(ctypes.byref(params), ctypes.byref(sz), None, None, None, None, None, None,
+                                      None), "letkf_domain_tables")
+    out = {"own_off": np.zeros(sz.n_dom + 1, np.int32), "own": np.zeros(sz.own_total, np.int32),
+           "obs_off": np.zeros(sz.n_dom + 1, np.int32), "obs_sub": np.zeros(sz.obs_total, np.int32),
+           "halo_off": np.zeros(sz.n_dom + 1, np.int32), "halo": np.zeros(sz.halo_total, np.int32),
+           "block": np.zeros(sz.n_dom, np.int32)}
+    _check(load().letkf_domain_tables(ctypes.byref(params), ctypes.byref(sz),
+                                      *[out[k].ctypes.data for k in ("own_off", "own", "obs_off", "obs_sub",
+                                                                      "halo_off", "halo", "block")]),
+           "letkf_domain_tables")
+    out.update({f: getattr(sz, f) for f, _ in letkf_domain_sizes._fields_})
+    return out
 
 
 def letkf_footprint(params: letkf_params) -> int:

@@ -95,7 +95,8 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
     h.own_off = {0};
     h.obs_off = {0};
     h.halo_off = {0};
-    h.own.clear(); h.obs_sub.clear(); h.obs_corner.clear(); h.halo.clear();
+    h.own.clear(); h.obs_sub.clear(); h.obs_corner.clear(); h.halo.clear(); h.block.clear();
+    h.blocks_per_side = nb;
     h.n_loc_max = h.p_loc_max = h.n_h_max = 0;
     std::vector<double> cost;
     for (int I = 0; I < nb; ++I) {
@@ -140,6 +141,7 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
                 }
                 corners.push_back(packed);
             }
+            h.block.push_back(I * nb + J);
             for (int k : owned) h.own.push_back(k);
             for (size_t t = 0; t < subs.size(); ++t) {
                 h.obs_sub.push_back(subs[t]);
@@ -363,6 +365,35 @@ int letkf_footprint(const letkf_params* p, unsigned long long* bytes) {
     build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
     if (h.n_act == 0 || h.own_off.size() < 2) return LETKF_EINVAL;
     *bytes = footprint_bytes(p, h);
+    return LETKF_OK;
+}
+
+int letkf_domain_tables(const letkf_params* p, letkf_domain_sizes* sz, int* own_off, int* own, int* obs_off,
+                        int* obs_sub, int* halo_off, int* halo, int* block) {
+    if (!p || !sz) return LETKF_EINVAL;
+    if (validate(p)) return LETKF_EINVAL;
+    letkf::HostModel h;
+    build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    const int nd = (int)h.own_off.size() - 1;
+    if (h.n_act == 0 || nd < 1) return LETKF_EINVAL;
+    sz->n_sub = p->n_sub;
+    sz->n_act = h.n_act;
+    sz->n_subv = h.n_subv;
+    sz->n_dom = nd;
+    sz->blocks_per_side = h.blocks_per_side;
+    sz->own_total = (int)h.own.size();
+    sz->obs_total = (int)h.obs_sub.size();
+    sz->halo_total = (int)h.halo.size();
+    auto put = [](int* dst, const std::vector<int>& v) {
+        if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(int));
+    };
+    put(own_off, h.own_off);
+    put(own, h.own);
+    put(obs_off, h.obs_off);
+    put(obs_sub, h.obs_sub);
+    put(halo_off, h.halo_off);
+    put(halo, h.halo);
+    put(block, h.block);
     return LETKF_OK;
 }
 

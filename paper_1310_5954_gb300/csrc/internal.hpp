@@ -42,6 +42,8 @@ struct HostModel {
     std::vector<int> sub_rc, act_rc;         // valid index -> (r, c)
     int n_act = 0, n_subv = 0;
     std::vector<int> own_off, own, obs_off, obs_sub, obs_corner, halo_off, halo, order;
+    std::vector<int> block;                  // block index I * blocks_per_side + J of each domain
+    int blocks_per_side = 0;
     int n_loc_max = 0, p_loc_max = 0, n_h_max = 0;
 };
 
