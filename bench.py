@@ -535,9 +535,11 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
         "roofline": roof,
-        # main-stream stages (profiled) plus, for a dense noise factor, the side stream's normals kernel
+        # main-stream stages (profiled) plus the side stream's noise draw for the next frame: in
+        # mixed precision normals, tensor-core product and partial-sum kernels; in FP32 the normals
+        # kernel (the GEMM is cuBLAS's)
         "gpu_launches": int(K * sum(v[1] for v in prof.values()) / max(args.profile_steps, 1))
-                        + (K if args.path == "fused" else 0),
+                        + (K * (3 if precision == "mixed" else 1) if args.path == "fused" else 0),
         "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items()},
         "clocks": clk, "device_status": status,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
