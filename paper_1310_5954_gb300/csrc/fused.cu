@@ -71,6 +71,7 @@ struct SysDesc {
 struct Ctrl {
     uint64_t bar_load;
     uint64_t bar_mma;
+    uint64_t bar_mma2;   // second product of a Newton-Schulz step, issued from another warp
     uint32_t tmem_base;
     int item;            // global work item (over all systems of the batch)
     int sys;             // its system
@@ -130,11 +131,15 @@ __device__ __forceinline__ void issue_product(uint32_t d_tmem, const unsigned ch
     const unsigned char* xs[3] = {xh, xh, xl};
     const unsigned char* ws[3] = {wh, wl, wh};
     uint32_t acc = first_term > 0 ? 1u : 0u;
+    // consecutive K steps differ only in the start-address field (bits 0-13, in 16-byte units)
+    const uint64_t x_inc = 256u >> 4, w_inc = w_step >> 4;
     for (int t = first_term; t < nterms; ++t) {
-        const uint32_t xa = smem_u32(xs[t]), wa = smem_u32(ws[t]);
+        uint64_t xd = sdesc(smem_u32(xs[t]), 128u, x_sbo), wd = sdesc(smem_u32(ws[t]), w_lbo, w_sbo);
         for (int ks = 0; ks < (K >> 4); ++ks) {
-            mma_bf16(d_tmem, sdesc(xa + ks * 256u, 128u, x_sbo), sdesc(wa + ks * w_step, w_lbo, w_sbo), idesc, acc);
+            mma_bf16(d_tmem, xd, wd, idesc, acc);
             acc = 1;
+            xd += x_inc;
+            wd += w_inc;
         }
     }
 }
@@ -152,6 +157,25 @@ __device__ bool wait_all(Ctrl* ctl, uint64_t* bar, uint32_t parity, int* status)
     __syncthreads();
     if (ctl->abort) return false;
     while (!mbar_try_wait(bar, parity)) {
+    }
+    return true;
+}
+
+// wait_all for two barriers (two products issued by different threads).
+__device__ bool wait_all2(Ctrl* ctl, uint32_t p1, uint32_t p2, int* status) {
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait_bounded(&ctl->bar_mma, p1, WAIT_CYCLES) &&
+                        mbar_wait_bounded(&ctl->bar_mma2, p2, WAIT_CYCLES);
+        if (!ok) {
+            atomicOr(status, ST_TIMEOUT);
+            ctl->abort = 1;
+        }
+    }
+    __syncthreads();
+    if (ctl->abort) return false;
+    while (!mbar_try_wait(&ctl->bar_mma, p1)) {
+    }
+    while (!mbar_try_wait(&ctl->bar_mma2, p2)) {
     }
     return true;
 }
@@ -800,6 +824,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
     if (tid == 0) {
         mbar_init(&ctl->bar_load, 1);
         mbar_init(&ctl->bar_mma, 1);
+        mbar_init(&ctl->bar_mma2, 1);
         ctl->abort = 0;
         fence_mbar_init();
     }
@@ -811,7 +836,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ctl->tmem_base;
-    uint32_t ph_load = 0, ph_mma = 0;
+    uint32_t ph_load = 0, ph_mma = 0, ph_mma2 = 0;
     // a launch that follows this kernel through a programmatic edge may start now (it does not
     // read what this kernel writes)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1067,14 +1092,20 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
+            // the two products are issued by threads of different warps, so their issue loops
+            // (one tcgen05.mma per K step and BF16 term) overlap
             if (tid == 0) {
                 tc_fence_after();
                 issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
+                mma_commit(&ctl->bar_mma);
+            } else if (tid == 32) {
+                tc_fence_after();
                 issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
-                mma_commit(&ctl->bar_mma);   // one commit covers both products
+                mma_commit(&ctl->bar_mma2);
             }
-            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) { ok = false; break; }
+            if (!wait_all2(ctl, ph_mma, ph_mma2, A.status)) { ok = false; break; }
             ph_mma ^= 1;
+            ph_mma2 ^= 1;
             tc_fence_after();
 #pragma unroll 1
             for (int q8 = 0; q8 < nq; ++q8) {
