@@ -291,6 +291,16 @@ const char* letkf_stage_name(int stage);
 int letkf_umma_selftest(const float* a_dev, const float* b_dev, float* d_dev, int n, int k, int terms,
                         int b_layout, void* stream);
 
+/*
+ * Self-test of the bounded device-side wait (diagnostic; the paper has no counterpart).  Every
+ * kernel of the library waits on its mbarriers for a bounded number of SM cycles, then latches
+ * LETKF_ETIMEOUT and returns instead of hanging.  This runs that wait in one CTA on a barrier
+ * that completes only if arrive = 1, with the given limit (1000 .. 2e9 cycles), on `stream`, and
+ * synchronises: LETKF_OK when the barrier completed, LETKF_ETIMEOUT when the limit ran out (the
+ * CUDA context stays usable), LETKF_EINVAL for other arguments.
+ */
+int letkf_wait_selftest(long long limit_cycles, int arrive, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,7 @@ _SIGS = {
     "letkf_umma_selftest": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            _VP]),
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "letkf_wait_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _VP]),
     "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
     "letkf_domain_tables": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(letkf_domain_sizes),
                                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -375,6 +376,11 @@ def letkf_server_replay(server: int, sys_ids, t_ns, y_ptrs, sigma=None) -> int:
     refused = ctypes.c_int()
     _check(load().letkf_server_replay(server, n, s, t, y, sg, ctypes.byref(refused)), "letkf_server_replay")
     return refused.value
+
+
+def letkf_wait_selftest(limit_cycles: int, arrive: int, stream: int = 0) -> int:
+    """Status of the bounded-wait self-test (no raise): LETKF_OK or LETKF_ETIMEOUT."""
+    return load().letkf_wait_selftest(int(limit_cycles), int(arrive), stream or None)
 
 
 def declared_functions(header: str) -> list:

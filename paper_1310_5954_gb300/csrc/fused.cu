@@ -1408,6 +1408,21 @@ __global__ void __launch_bounds__(FT, 1) umma_selftest_kernel(const float* __res
     if (warp == 0) tmem_dealloc(tbase, 256);
 }
 
+// The bounded mbarrier wait every kernel of the library uses, on a barrier that completes only if
+// `arrive` is set: thread 0 waits at most `limit` SM cycles, then latches ST_TIMEOUT and returns.
+__global__ void wait_selftest_kernel(long long limit, int arrive, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 32 && arrive)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit)) atomicOr(status, ST_TIMEOUT);
+    __syncthreads();
+}
+
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 struct FusedLayout {
@@ -1833,5 +1848,21 @@ extern "C" int letkf_umma_selftest(const float* A, const float* B, float* D, int
     cudaError_t e2 = cudaStreamSynchronize((cudaStream_t)stream);
     cudaFree(st);
     if (e != cudaSuccess || e2 != cudaSuccess) return LETKF_ECUDA;
+    return h ? LETKF_ETIMEOUT : LETKF_OK;
+}
+
+extern "C" int letkf_wait_selftest(long long limit_cycles, int arrive, void* stream) {
+    using namespace letkf;
+    if (limit_cycles < 1000 || limit_cycles > 2000000000LL || (arrive != 0 && arrive != 1)) return LETKF_EINVAL;
+    int* st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) return LETKF_ENOMEM;
+    cudaMemsetAsync(st, 0, sizeof(int), (cudaStream_t)stream);
+    wait_selftest_kernel<<<1, 64, 0, (cudaStream_t)stream>>>(limit_cycles, arrive, st);
+    int h = 0;
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e1 = cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    cudaError_t e2 = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(st);
+    if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) return LETKF_ECUDA;
     return h ? LETKF_ETIMEOUT : LETKF_OK;
 }

@@ -53,3 +53,21 @@ def test_umma_rejects_bad_shapes():
     assert _lib.letkf_umma_selftest(1, 1, 1, 16, 144, 1) == _lib.LETKF_EINVAL
     assert _lib.letkf_umma_selftest(1, 1, 1, 16, 16, 2) == _lib.LETKF_EINVAL
     assert _lib.letkf_umma_selftest(1, 1, 1, 16, 16, 1, 2) == _lib.LETKF_EINVAL
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """A device-side wait on a barrier nothing completes ends after its limit (~1 ms here) with
+    LETKF_ETIMEOUT, not a hang; the context keeps working: the same wait with the arrival
+    completes, and a filter step afterwards runs clean."""
+    import time
+    t0 = time.perf_counter()
+    assert _lib.letkf_wait_selftest(2_000_000, 0) == _lib.LETKF_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert _lib.letkf_wait_selftest(2_000_000, 1) == _lib.LETKF_OK
+    assert _lib.letkf_wait_selftest(10, 1) == _lib.LETKF_EINVAL
+    from _gpu_common import gpu_filter, slopes
+    y, _ = slopes("tiny-8x8", 2)
+    f = gpu_filter("tiny-8x8", "mixed", "fused")
+    f.step(torch.as_tensor(y[0], dtype=torch.float32, device="cuda"))
+    assert f.sync() == 0
+    f.close()
