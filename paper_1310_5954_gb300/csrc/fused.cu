@@ -1023,31 +1023,63 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         }
         const float s_scale = 1.f + sqrtf(fro) / c;
         const float inv_cs = 1.f / (c * s_scale);
-#pragma unroll 1
-        for (int q8 = 0; q8 < nq; ++q8) {
-            float g[8], yv[8], zv[8];
-            tmem_ld8(tl + TM_G + 8 * q8, g);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = col0 + 8 * q8 + u;
-                const bool in = row < m && j < m;
-                const float id = (row == j) ? 1.f : 0.f;
-                yv[u] = in ? (id + g[u] / c) / s_scale : 0.f;
-                zv[u] = in ? id : 0.f;
-            }
-            if (row < NP) {
-                store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
-            }
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z
-        bool z_in_tmem = false;
-        float rn_prev = 3.0e38f;
-        int it = 0;
+        // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
+        //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
+        //      Z_1 = T_0: one pass over G writes Y_0, T_0 (also as Z_1) and the residual.
+        int z_state = 1;     // where Z is: 0 identity, 1 shared memory only (Z_1 = T_0), 2 also TMEM
+        int it = 1;
         bool ok = true;
+        float rn_prev;
+        {
+            float r2 = 0.f;
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float g[8], yv[8], tv[8];
+                tmem_ld8(tl + TM_G + 8 * q8, g);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = col0 + 8 * q8 + u;
+                    const bool in = row < m && j < m;
+                    const float id = (row == j) ? 1.f : 0.f;
+                    yv[u] = in ? (id + g[u] / c) / s_scale : 0.f;
+                    const float rr = id - yv[u];
+                    if (in) r2 += rr * rr;
+                    tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
+                }
+                if (row < NP) {
+                    store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                    store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
+                    store8(Zh, Zl, row, col0 + 8 * q8, NP, tv, true);
+                }
+            }
+            rn_prev = sqrtf(block_sum(ctl, r2));
+        }
+        if (rn_prev < 2e-6f * (float)m) {
+            z_state = 0;     // converged at once: Z = I
+            it = 0;
+        } else {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
+                mma_commit(&ctl->bar_mma);
+            }
+            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
+            ph_mma ^= 1;
+            tc_fence_after();
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float yv[8];
+                tmem_ld8(tl + TM_Y + 8 * q8, yv);
+                if (row < NP) store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (z_state != 0)
         for (; it < A.max_it; ++it) {
             if (tid == 0) {
                 tc_fence_after();
@@ -1124,7 +1156,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
                 }
             }
-            z_in_tmem = true;
+            z_state = 2;
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
@@ -1137,8 +1169,20 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         // ---- 4. mean weights w_bar = Z (Z b) / (c s), refined against the exact operator
         // 8 columns of this thread's half-row of Z = A_s^(-1/2)
         auto zrow = [&](int q8, float (&zv)[8]) {
-            if (z_in_tmem) {
+            if (z_state == 2) {
                 tmem_ld8(tl + TM_Z + 8 * q8, zv);
+            } else if (z_state == 1) {     // high + low BF16 parts of the shared-memory operand
+                const uint32_t off = op_offset(row < NP ? row : 0, col0 + 8 * q8, NP);
+                const uint4 h = *reinterpret_cast<const uint4*>(Zh + off);
+                const uint4 l = *reinterpret_cast<const uint4*>(Zl + off);
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[u]));
+                    const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&lw[u]));
+                    zv[2 * u] = row < NP ? fh.x + fl.x : 0.f;
+                    zv[2 * u + 1] = row < NP ? fh.y + fl.y : 0.f;
+                }
             } else {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) zv[u] = (row == col0 + 8 * q8 + u && row < m) ? 1.f : 0.f;
