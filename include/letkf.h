@@ -12,7 +12,8 @@
  *   state     x = [phi_k ; phi_{k-1}] on the valid actuators (Fried geometry),
  *             n = 2 * n_act, rows: all actuators of the first instant, then the
  *             second, valid actuators numbered in row-major grid order;
- *   dynamics  x_{k+1} = A1 x_k + [v_k ; 0],  A1 = [[a I, 0], [I, 0]],  v ~ N(0, Q);
+ *   dynamics  x_{k+1} = A1 x_k + [v_k ; 0],  A1 = [[a I, a2 I], [I, 0]] (AR(2); a2 = 0: AR(1)),
+ *             v ~ N(0, Q);
  *   slopes    y_k = C x_k + w_k,  C = [0 D] (obs_block = 1) or [D 0] (obs_block = 0),
  *             D the Fried difference operator, p = 2 * n_subv, all x-slopes then
  *             all y-slopes of the valid subapertures in row-major grid order;
@@ -99,6 +100,10 @@ typedef struct letkf_params {
                                        process noise) */
     int device;                     /* CUDA device ordinal */
     void* stream;                   /* cudaStream_t borrowed from the caller (NULL: default) */
+    double ar2_a;                   /* AR coefficient a2 of the second instant (Sect. 2.1, "AR 1 or
+                                       AR 2"): A1 = [[a I, a2 I], [I, 0]]; 0 is the AR(1) model.
+                                       The AR(2) must be stationary: |a2| < 1, a + a2 < 1,
+                                       a2 - a < 1 (for a2 = 0: |a| < 1) */
 } letkf_params;
 
 typedef struct letkf_info {

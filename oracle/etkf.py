@@ -79,11 +79,15 @@ def letkf_analysis(Xf: np.ndarray, y: np.ndarray, C, sigma: float, domains: List
     return Xa
 
 
-def forecast(Xa: np.ndarray, a: float, V: np.ndarray) -> np.ndarray:
-    """AR(1) forecast of every member with the two-instant companion matrix A1."""
+def forecast(Xa: np.ndarray, a: float, V: np.ndarray, a2: float = 0.0) -> np.ndarray:
+    """Forecast of every member with the two-instant companion matrix of the AR model (Sect. 2.1,
+    "AR 1 or AR 2"): A1 = [[a I, a2 I], [I, 0]], i.e. phi_{k+1} = a phi_k + a2 phi_{k-1} + v_k;
+    a2 = 0 is the AR(1) model."""
     n_act = Xa.shape[0] // 2
     Xf = np.empty_like(Xa)
     Xf[:n_act] = a * Xa[:n_act] + V
+    if a2 != 0.0:
+        Xf[:n_act] += a2 * Xa[n_act:]
     Xf[n_act:] = Xa[:n_act]
     return Xf
 
@@ -101,8 +105,9 @@ class OracleFilter:
     def __init__(self, geom: Geometry, domains: Optional[List[Domain]], m: int, a: float,
                  sigma: float, seed: int, L: Optional[np.ndarray] = None, q_white: float = 0.0,
                  obs_block: int = 1, X0: Optional[np.ndarray] = None,
-                 L_stat: Optional[np.ndarray] = None):
+                 L_stat: Optional[np.ndarray] = None, a2: float = 0.0):
         self.geom, self.domains, self.m, self.a = geom, domains, m, float(a)
+        self.a2 = float(a2)
         self.sigma, self.seed, self.L, self.q_white = float(sigma), int(seed), L, float(q_white)
         self.L_stat = L_stat
         self.C = sparse_observation(geom, obs_block)
@@ -116,14 +121,18 @@ class OracleFilter:
         """Initial ensemble (Sect. 2.2), one AR(1) pair per member: the second block is drawn
         from the stationary phase covariance, block2 = L_stat xi0 (L_stat defaults to
         L / sqrt(1 - a^2), or q_white / sqrt(1 - a^2) for white noise), and the first block
-        follows the model, block1 = a block2 + L xi1."""
+        follows the model, block1 = a block2 + L xi1 (for AR(2) the stationary variance of the
+        AR(2) model replaces 1 / (1 - a^2))."""
         na = self.geom.n_act
         xi2 = philox.normals(self.seed, 0, 0, self.m, na)
         xi1 = philox.normals(self.seed, 0, 1, self.m, na)
         if self.L_stat is not None:
             b2 = self.L_stat @ xi2
         else:
-            b2 = self._noise(xi2) / np.sqrt(1.0 - self.a ** 2)
+            # stationary variance of the AR model with unit innovations: for AR(2)
+            # (1 - a2) / ((1 + a2) ((1 - a2)^2 - a^2)), i.e. 1 / (1 - a^2) when a2 = 0
+            a, a2 = self.a, self.a2
+            b2 = self._noise(xi2) * np.sqrt((1.0 - a2) / ((1.0 + a2) * ((1.0 - a2) ** 2 - a * a)))
         b1 = self.a * b2 + self._noise(xi1)
         return np.vstack([b1, b2])
 
@@ -142,7 +151,7 @@ class OracleFilter:
     def forecast(self, V: Optional[np.ndarray] = None) -> None:
         if V is None:
             V = self.perturbation(self.frame)
-        self.X = forecast(self.X, self.a, V)
+        self.X = forecast(self.X, self.a, V, self.a2)
         self.frame += 1
 
     def step(self, y: np.ndarray, sigma: Optional[float] = None,

@@ -40,6 +40,7 @@ class letkf_params(ctypes.Structure):
         ("seed", ctypes.c_ulonglong),
         ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("ar2_a", ctypes.c_double),
     ]
 
 

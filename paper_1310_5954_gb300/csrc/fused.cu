@@ -60,6 +60,7 @@ struct SysDesc {
     int dual;            // analysis in observation space (m >= 128)
     int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, RA, item0;
     float inv_sigma, a, q_white;
+    float a2;            // AR coefficient of the second instant (0: AR(1))
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
     uint32_t frame;
@@ -216,7 +217,7 @@ __device__ __forceinline__ void simt_rows(const SysDesc& A, int e0, int n_own) {
                     normals4<float>(A.seed, 1u, A.frame, (uint32_t)i, (uint32_t)(j >> 2), z);
                     v = A.q_white * z[j & 3];
                 }
-                n1 = A.a * a1 + v;
+                n1 = A.a * a1 + A.a2 * x2[i] + v;
                 o1[i] = n1;
                 o2[i] = a1;
             }
@@ -233,7 +234,7 @@ __device__ __forceinline__ void issue_loads(const SysDesc& A, int d, unsigned ch
     float* XE = reinterpret_cast<float*>(smem + A.off_xe);
     const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
     const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
-    const int n_e = A.with_forecast ? n_own : 2 * n_own;
+    const int n_e = (A.with_forecast && A.a2 == 0.f) ? n_own : 2 * n_own;   // AR(2) needs both instants
     const uint32_t rb = (uint32_t)A.m_pad * 4u;
     mbar_arrive_expect_tx(bar, rb * (uint32_t)(n_h + n_e));
     for (int j = 0; j < n_h; ++j)
@@ -336,7 +337,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const int o0 = A.tab.obs_off[d], n_obs = A.tab.obs_off[d + 1] - o0;
     const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
     const int P = 2 * n_obs;
-    const int n_e = A.with_forecast ? n_own : 2 * n_own;
+    const int n_e = (A.with_forecast && A.a2 == 0.f) ? n_own : 2 * n_own;   // AR(2) needs both instants
     // p-space matrices: NP x NP, this thread's TMEM lane `row`, columns col0 .. col0 + NP/2
     const int half = NP / 2, nq = half / 8, col0 = hh * half;
     const uint32_t tl = tbase + lane_off + (uint32_t)col0;
@@ -771,12 +772,30 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const float p3mean = mine ? (vtmp[row] + vtmp[128 + row]) / (float)m : 0.f;
     const float shift = mine ? uvec[row] : 0.f;
     __syncthreads();
+    // AR(2) forecast: second-instant rows hand their analysis to the first-instant rows
+    const bool ar2 = A.with_forecast && A.a2 != 0.f;
+    float* x2buf = reinterpret_cast<float*>(big);
+    if (ar2) {
+#pragma unroll 1
+        for (int q8 = 0; q8 < mq; ++q8) {
+            float dv[8];
+            tmem_ld8(tlm + TM_Y + 8 * q8, dv);
+            if (mine && row >= n_own)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = mcol0 + 8 * q8 + u;
+                    if (j < m) x2buf[(row - n_own) * A.m_pad + j] = A.X[(size_t)grow * A.m_pad + j] + shift - (dv[u] - p3mean);
+                }
+        }
+        __syncthreads();
+    }
+    const bool writes = mine && !(ar2 && row >= n_own);
     float psum = 0.f;
 #pragma unroll 1
     for (int q8 = 0; q8 < mq; ++q8) {
         float dv[8];
         tmem_ld8(tlm + TM_Y + 8 * q8, dv);
-        if (!mine) continue;
+        if (!writes) continue;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int j = mcol0 + 8 * q8 + u;
@@ -791,7 +810,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
                         normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
                         v = A.q_white * zz[jact & 3];
                     }
-                    const float n1 = A.a * xa + v;
+                    const float n1 = A.a * xa + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + v;
                     A.Xo[(size_t)jact * A.m_pad + j] = n1;
                     A.Xo[(size_t)(A.n_act + jact) * A.m_pad + j] = xa;
                     psum += n1;
@@ -804,7 +823,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     if (A.with_forecast) {
         vtmp[hh * 128 + row] = psum;
         __syncthreads();
-        if (hh == 0 && mine && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
+        if (hh == 0 && writes && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
     }
     tc_fence_before();
     __syncthreads();
@@ -891,7 +910,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         const int o0 = A.tab.obs_off[d], n_obs = A.tab.obs_off[d + 1] - o0;
         const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
         const int p_loc = 2 * n_obs;
-        const int n_e = A.with_forecast ? n_own : 2 * n_own;
+        const int n_e = (A.with_forecast && A.a2 == 0.f) ? n_own : 2 * n_own;   // AR(2) needs both instants
         if (n_obs == 0) {
             simt_rows(A, e0, n_own);
             __syncthreads();
@@ -1322,12 +1341,29 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         }
         const float shift = mine ? xe_mean[row] + uvec[row] - (vtmp[row] + vtmp[128 + row]) / (float)m : 0.f;
         __syncthreads();
+        // AR(2) forecast: the rows of the second instant leave their analysis in shared memory (the
+        // operand buffers are free now) for the first-instant rows of the same actuators
+        const bool ar2 = A.with_forecast && A.a2 != 0.f;
+        float* x2buf = reinterpret_cast<float*>(big);
+        if (ar2) {
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float dv[8];
+                tmem_ld8(tl + TM_P + 8 * q8, dv);
+                if (mine && row >= n_own)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (col0 + 8 * q8 + u < m) x2buf[(row - n_own) * A.m_pad + col0 + 8 * q8 + u] = shift + dv[u];
+            }
+            __syncthreads();
+        }
+        const bool writes = mine && !(ar2 && row >= n_own);
         float psum = 0.f;
 #pragma unroll 1
         for (int q8 = 0; q8 < nq; ++q8) {
             float dv[8];
             tmem_ld8(tl + TM_P + 8 * q8, dv);
-            if (!mine) continue;
+            if (!writes) continue;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int j = col0 + 8 * q8 + u;
@@ -1342,7 +1378,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                             normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
                             v = A.q_white * zz[jact & 3];
                         }
-                        const float n1 = A.a * xa + v;
+                        const float n1 = A.a * xa + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + v;
                         A.Xo[(size_t)jact * A.m_pad + j] = n1;
                         A.Xo[(size_t)(A.n_act + jact) * A.m_pad + j] = xa;
                         psum += n1;
@@ -1355,7 +1391,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         if (A.with_forecast) {
             vtmp[hh * 128 + row] = psum;
             __syncthreads();
-            if (hh == 0 && mine && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
+            if (hh == 0 && writes && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
         }
         tc_fence_before();
         __syncthreads();
@@ -1637,6 +1673,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->scratch_stride = c->scratch_stride;
     S->inv_sigma = (float)(1.0 / c->sigma);
     S->a = (float)c->a;
+    S->a2 = (float)c->a2;
     S->q_white = (float)c->q_white;
     S->with_forecast = f.with_forecast;
     S->gram_terms = c->precision == LETKF_PREC_MIXED ? 1 : 3;

@@ -210,7 +210,8 @@ void free_all(letkf_ctx* c) {
 
 int validate(const letkf_params* p) {
     if (p->n_sub < 1 || p->n_sub > 1024 || p->m < 2 || p->m > 256 || p->dom_sub < 1 || p->halo < 0 ||
-        !(p->sigma > 0) || !(std::fabs(p->ar1_a) < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
+        !(p->sigma > 0) || !(std::fabs(p->ar2_a) < 1.0) || !(p->ar1_a + p->ar2_a < 1.0) ||
+        !(p->ar2_a - p->ar1_a < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
         p->precision < 0 || p->precision > 2 || p->path < 0 || p->path > 1 || p->q_white < 0 ||
         !(p->obstruction >= 0 && p->obstruction < 1))
         return LETKF_EINVAL;
@@ -259,7 +260,7 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     if (validate(p)) return LETKF_EINVAL;
     c->n_sub = p->n_sub; c->m = p->m; c->dom_sub = p->dom_sub; c->halo = p->halo;
     c->precision = p->precision; c->path = p->path; c->obs_block = p->obs_block; c->device = p->device;
-    c->a = p->ar1_a; c->sigma = p->sigma; c->q_white = p->q_white; c->seed = p->seed;
+    c->a = p->ar1_a; c->a2 = p->ar2_a; c->sigma = p->sigma; c->q_white = p->q_white; c->seed = p->seed;
     c->stream = (cudaStream_t)p->stream;
     const int eb = c->precision == LETKF_PREC_FP64 ? 8 : 4;
     c->m_pad = (eb == 8) ? ((c->m + 1) / 2) * 2 : ((c->m + 3) / 4) * 4;

@@ -53,7 +53,7 @@ struct letkf_ctx {
     // parameters
     int n_sub = 0, m = 0, m_pad = 0, dom_sub = 0, halo = 0;
     int precision = 0, path = 0, obs_block = 1, device = 0;
-    double a = 0, sigma = 0, q_white = 0;
+    double a = 0, a2 = 0, sigma = 0, q_white = 0;
     unsigned long long seed = 0;
     cudaStream_t stream = nullptr;
     int sms = 0;

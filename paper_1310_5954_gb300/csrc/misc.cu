@@ -70,7 +70,7 @@ __global__ void normals_kernel(O* __restrict__ out, int ld, int n_act, int m, un
 // vmode 0: v from V (ld vld); 1: white noise q * xi drawn inline; 2: no perturbation.
 template <typename T>
 __global__ void forecast_kernel(T* __restrict__ X, const T* __restrict__ V, int vld, int vmode, T q_white,
-                                T a, int n_act, int m, int m_pad, T* __restrict__ xpred,
+                                T a, T a2, int n_act, int m, int m_pad, T* __restrict__ xpred,
                                 const int* __restrict__ frame_bad, int check_bad, unsigned long long seed,
                                 uint32_t frame) {
     const bool skip = check_bad && *frame_bad;
@@ -91,8 +91,9 @@ __global__ void forecast_kernel(T* __restrict__ X, const T* __restrict__ V, int 
                     normals4<T>(seed, 1u, frame, (uint32_t)i, (uint32_t)(j >> 2), z);
                     v = q_white * z[j & 3];
                 }
+                const T v2 = x2[i];
                 x2[i] = v1;
-                v1 = a * v1 + v;
+                v1 = a * v1 + a2 * v2 + v;
                 x1[i] = v1;
             }
             s += v1;
@@ -256,12 +257,13 @@ int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analys
     prof_begin(c, STAGE_FORECAST);
     if (c->precision == LETKF_PREC_FP64)
         forecast_kernel<double><<<g, 256, 0, c->stream>>>((double*)c->X[c->cur], (const double*)Vp, vld, vmode,
-                                                          c->q_white, c->a, c->n_act, c->m, c->m_pad,
+                                                          c->q_white, c->a, c->a2, c->n_act, c->m, c->m_pad,
                                                           (double*)xpred, c->d_frame_bad, in_analysis, c->seed,
                                                           (uint32_t)c->frame);
     else
         forecast_kernel<float><<<g, 256, 0, c->stream>>>((float*)c->X[c->cur], (const float*)Vp, vld, vmode,
-                                                         (float)c->q_white, (float)c->a, c->n_act, c->m, c->m_pad,
+                                                         (float)c->q_white, (float)c->a, (float)c->a2, c->n_act, c->m,
+                                                         c->m_pad,
                                                          (float*)xpred, c->d_frame_bad, in_analysis, c->seed,
                                                          (uint32_t)c->frame);
     prof_end(c);
@@ -269,7 +271,8 @@ int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analys
 }
 
 // Initial ensemble (Sect. 2.2): second instant = P0 xi0, first = a * second + L xi1, with
-// xi0, xi1 the Philox draws (stream 0, frames 0 and 1).  P0 defaults to L / sqrt(1 - a^2).
+// xi0, xi1 the Philox draws (stream 0, frames 0 and 1).  P0 defaults to L times the stationary
+// standard deviation of the AR model (1 / sqrt(1 - a^2) for AR(1)).
 int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
     const int na = c->n_act, m = c->m;
     const bool f64 = c->precision == LETKF_PREC_FP64;
@@ -326,7 +329,10 @@ int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
     int rc = LETKF_OK;
     if (cudaMalloc(&xi, (size_t)na * row) != cudaSuccess) return LETKF_ENOMEM;
     cudaMemset(xi, 0, (size_t)na * row);
-    const double sa = 1.0 / std::sqrt(1.0 - c->a * c->a);
+    // stationary standard deviation of the AR model with unit innovations (the default P0 scale):
+    // AR(2) gamma_0 = (1 - a2) / ((1 + a2) ((1 - a2)^2 - a^2)), which is 1 / (1 - a^2) for a2 = 0
+    const double a2 = c->a2;
+    const double sa = std::sqrt((1.0 - a2) / ((1.0 + a2) * ((1.0 - a2) * (1.0 - a2) - c->a * c->a)));
     void* X = c->X[0];
     void* X2 = static_cast<char*>(X) + (size_t)na * row;  // second instant rows
     const int nq = (na + 3) / 4;

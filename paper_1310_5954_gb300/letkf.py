@@ -23,7 +23,8 @@ _PATH = {"plain": _lib.LETKF_PATH_PLAIN, "fused": _lib.LETKF_PATH_FUSED}
 def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4, halo: int = 2,
                 obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
                 q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0, p0_sqrt: Optional[np.ndarray] = None,
-                precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1):
+                precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1,
+                ar2_a: float = 0.0):
     """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used)."""
     p = _lib.letkf_params()
     keep = []
@@ -51,6 +52,7 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
     p.precision = _PREC[precision]
     p.path = _PATH[path]
     p.seed = int(seed)
+    p.ar2_a = float(ar2_a)
     return p, keep
 
 
@@ -67,7 +69,8 @@ class LETKF:
                  obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
                  q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0,
                  p0_sqrt: Optional[np.ndarray] = None, precision: str = "fp32", path: str = "plain",
-                 seed: int = 0, obs_block: int = 1, device: Optional[int] = None, stream=None):
+                 seed: int = 0, obs_block: int = 1, device: Optional[int] = None, stream=None,
+                 ar2_a: float = 0.0):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -77,7 +80,8 @@ class LETKF:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p, keep = make_params(n_sub=n_sub, m=m, ar1_a=ar1_a, sigma=sigma, dom_sub=dom_sub, halo=halo,
                               obstruction=obstruction, sub_valid=sub_valid, q_sqrt=q_sqrt, q_white=q_white,
-                              p0_sqrt=p0_sqrt, precision=precision, path=path, seed=seed, obs_block=obs_block)
+                              p0_sqrt=p0_sqrt, precision=precision, path=path, seed=seed, obs_block=obs_block,
+                              ar2_a=ar2_a)
         self._keep = keep
         p.device = dev
         p.stream = self.stream.cuda_stream

@@ -11,10 +11,10 @@ both the CUDA path and the FP64 oracle consume its outputs unchanged.
 from .turbulence import (VKScreen, vk_phase_covariance, vk_structure_function_kolmogorov,
                          actuator_covariance_lag_table)
 from .wfs import FineGridSensor
-from .workloads import Workload, WORKLOADS, workload, serving_mix, TruthStream, compressed_frames
+from .workloads import Workload, WORKLOADS, workload, serving_mix, TruthStream, compressed_frames, yule_walker_ar2
 
 __all__ = [
     "VKScreen", "vk_phase_covariance", "vk_structure_function_kolmogorov",
     "actuator_covariance_lag_table", "FineGridSensor", "Workload", "WORKLOADS", "workload",
-    "serving_mix", "TruthStream", "compressed_frames",
+    "serving_mix", "TruthStream", "compressed_frames", "yule_walker_ar2",
 ]

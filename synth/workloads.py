@@ -35,7 +35,7 @@ class Workload:
     m: int                   # ensemble size
     dom_sub: int             # estimation-domain side, in subapertures
     halo: int                # observation halo, in subapertures
-    ar1_a: float             # AR(1) coefficient of the turbulence model
+    ar1_a: float             # AR coefficient of phi_k in the turbulence model
     sigma: float             # slope-noise std (rad per slope)
     tel_diam: float          # telescope diameter (m)
     d_over_r0: float
@@ -48,6 +48,7 @@ class Workload:
     obs_block: int = 1       # slopes observe the state's second block (one-frame sensor delay)
     q: int = 4               # fine samples per pitch in the truth sensor
     nonstationary: bool = False
+    ar2_a: float = 0.0       # AR coefficient of phi_{k-1} (0: AR(1) model)
 
     @property
     def pitch(self) -> float:
@@ -98,17 +99,37 @@ class Workload:
         of one phase instant at the given actuators ((n_act, 2) row, column positions)."""
         return self._chol(self._lag_gather(act_rc), jitter)
 
-    def process_noise_sqrt(self, act_rc: np.ndarray, jitter: float = 1e-8) -> np.ndarray:
-        """Lower-triangular L with L L^T = Q + eps I, Q the covariance of the AR(1) innovation
-        phi_{k+1} - a phi_k when the true phase is von Karman turbulence under frozen flow
-        at the workload's wind:  Q = (1 + a^2) S(0) - a (S(s) + S(s)^T),  S(s)_ij the
-        covariance between actuator i now and actuator j one frame (shift s) later."""
+    def _shift(self, frames: int = 1):
         v, ang = self.wind_at(0)
-        s = (v / self.frame_rate * math.cos(ang), v / self.frame_rate * math.sin(ang))
-        a = self.ar1_a
+        return (frames * v / self.frame_rate * math.cos(ang), frames * v / self.frame_rate * math.sin(ang))
+
+    def process_noise_sqrt(self, act_rc: np.ndarray, jitter: float = 1e-8) -> np.ndarray:
+        """Lower-triangular L with L L^T = Q + eps I, Q the covariance of the AR innovation
+        e = phi_{k+1} - a phi_k - a2 phi_{k-1} when the true phase is von Karman turbulence under
+        frozen flow at the workload's wind:
+            Q = (1 + a^2 + a2^2) S(0) - (a - a a2) (S(s) + S(s)^T) - a2 (S(2s) + S(2s)^T),
+        S(js)_ij the covariance between actuator i now and actuator j j frames (shift js) later
+        (a2 = 0: the AR(1) innovation (1 + a^2) S(0) - a (S(s) + S(s)^T))."""
+        a, a2 = self.ar1_a, self.ar2_a
         S0 = self._lag_gather(act_rc)
-        S1 = self._lag_gather(act_rc, s)
-        return self._chol((1.0 + a * a) * S0 - a * (S1 + S1.T), jitter)
+        S1 = self._lag_gather(act_rc, self._shift(1))
+        Q = (1.0 + a * a + a2 * a2) * S0 - (a - a * a2) * (S1 + S1.T)
+        if a2 != 0.0:
+            S2 = self._lag_gather(act_rc, self._shift(2))
+            Q = Q - a2 * (S2 + S2.T)
+        return self._chol(Q, jitter)
+
+    def ar2_fit(self, act_rc: np.ndarray):
+        """(a, a2) of the AR(2) model fitted to the frozen-flow turbulence: the Yule-Walker
+        equations on the phase autocovariance summed over the actuators, t_j = tr S(js)."""
+        t = [float(np.trace(self._lag_gather(act_rc, self._shift(j)))) for j in range(3)]
+        return yule_walker_ar2(*t)
+
+
+def yule_walker_ar2(t0: float, t1: float, t2: float):
+    """AR(2) coefficients from the autocovariances at lags 0, 1, 2: [[t0, t1], [t1, t0]] a = [t1, t2]."""
+    det = t0 * t0 - t1 * t1
+    return (t1 * t0 - t1 * t2) / det, (t0 * t2 - t1 * t1) / det
 
 
 def _wl(i, **kw) -> Workload:

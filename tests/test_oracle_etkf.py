@@ -132,6 +132,23 @@ def test_forecast_companion_matrix():
     assert np.allclose(etkf.forecast(Xa, 0.97, V), ref, atol=1e-14)
 
 
+def test_ar2_forecast_companion_matrix():
+    # A1 = [[a I, a2 I], [I, 0]] written out densely, element by element
+    rng = np.random.default_rng(9)
+    n_act, m, a, a2 = 7, 4, 1.55, -0.62
+    Xa = rng.standard_normal((2 * n_act, m))
+    V = rng.standard_normal((n_act, m))
+    A = np.zeros((2 * n_act, 2 * n_act))
+    for i in range(n_act):
+        A[i, i] = a
+        A[i, n_act + i] = a2
+        A[n_act + i, i] = 1.0
+    ref = A @ Xa
+    ref[:n_act] += V
+    assert np.allclose(etkf.forecast(Xa, a, V, a2), ref, atol=1e-14)
+    assert np.array_equal(etkf.forecast(Xa, a, V, 0.0), etkf.forecast(Xa, a, V))
+
+
 def test_dare_matches_scipy():
     from synth import workload
     w = workload("tiny-8x8")
@@ -214,3 +231,14 @@ def test_etkf_approaches_kf_as_members_grow():
     assert gaps[0] > gaps[1] > gaps[2] > -0.02
     assert gaps[2] < 0.25
     assert 1.3 < gaps[1] / gaps[2] < 3.0
+
+
+def test_ar2_stationary_variance_solves_the_lyapunov_equation():
+    # the default initial-ensemble scale: stationary variance of phi_{k+1} = a phi_k + a2 phi_{k-1} + e,
+    # against scipy's discrete Lyapunov solver on the 2 x 2 companion matrix
+    from scipy.linalg import solve_discrete_lyapunov
+    for a, a2 in [(0.99, 0.0), (1.6, -0.65), (1.2, -0.3)]:
+        F = np.array([[a, a2], [1.0, 0.0]])
+        P = solve_discrete_lyapunov(F, np.diag([1.0, 0.0]))
+        gamma0 = (1.0 - a2) / ((1.0 + a2) * ((1.0 - a2) ** 2 - a * a))
+        assert abs(P[0, 0] - gamma0) < 1e-10 * gamma0

@@ -65,3 +65,39 @@ def test_truth_stream_shapes_and_determinism():
     # frozen flow: consecutive frames differ by a small shift of the same screen
     d = np.std(a["phi_act"][1] - a["phi_act"][0])
     assert 0 < d < 0.5 * np.std(a["phi_act"][0])
+
+
+def test_ar2_process_noise_is_the_ar2_innovation_covariance():
+    import dataclasses
+    w = dataclasses.replace(workload("tiny-8x8"), ar1_a=1.6, ar2_a=-0.65)
+    rc = np.array([(r, c) for r in range(3) for c in range(3)])
+    L = w.process_noise_sqrt(rc, jitter=0.0)
+    P = rc[:, ::-1] * w.pitch
+    s = np.array([w.wind / w.frame_rate, 0.0])
+    a, a2 = w.ar1_a, w.ar2_a
+    # brute force: e = phi_{k+1} - a phi_k - a2 phi_{k-1} with phi_{k+j}(x) = phi_k(x - j s)
+    cov = lambda u, v: vk_phase_covariance(np.array([np.linalg.norm(u - v)]), w.r0, w.L0)[0]
+    coef = [1.0, -a, -a2]           # weights of phi_{k+1}, phi_k, phi_{k-1}
+    Q = np.zeros((9, 9))
+    for i in range(9):
+        for j in range(9):
+            Q[i, j] = sum(coef[p] * coef[q] * cov(P[i] - (1 - p) * s, P[j] - (1 - q) * s)
+                          for p in range(3) for q in range(3))
+    assert np.allclose(L @ L.T, Q, rtol=1e-8, atol=1e-12)
+
+
+def test_yule_walker_recovers_a_known_ar2_process():
+    from synth import yule_walker_ar2
+    a1, a2 = 1.5, -0.6
+    # autocovariances of x_k = a1 x_{k-1} + a2 x_{k-2} + e_k (unit e): closed form
+    g0 = (1 - a2) / ((1 + a2) * ((1 - a2) ** 2 - a1 ** 2))
+    g1 = a1 * g0 / (1 - a2)
+    g2 = a1 * g1 + a2 * g0
+    b1, b2 = yule_walker_ar2(g0, g1, g2)
+    assert abs(b1 - a1) < 1e-12 and abs(b2 - a2) < 1e-12
+    # the fit of the frozen-flow workload is a stable AR(2)
+    from oracle import geometry
+    w = workload("vlt-40x40")
+    g = geometry.make_geometry(w.n_sub, w.obstruction)
+    f1, f2 = w.ar2_fit(g.act_rc)
+    assert abs(f2) < 1 and f1 + f2 < 1 and f2 - f1 < 1
