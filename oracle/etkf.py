@@ -23,7 +23,10 @@ forecast (G = 0 gives w_bar = 0, T = I).
 Forecast (Sect. 2.1, AR(1) on a two-instant state): A1 = [[a I, 0], [I, 0]],
 x_f(k+1) = A1 x_a(k) + [v_k; 0] per member, v_k = L xi_k with Q = L L^T.
 One filter step takes y_k, runs the analysis, then the forecast, and returns
-x_hat(k+1|k) (Eq. 1 is the prediction form).
+x_hat(k+1|k) (Eq. 1 is the prediction form).  With differential-piston removal (module
+`piston`), the step then fits one piston per domain to the slope residual of x_hat(k+1|k)
+against y_k and adds it to the returned prediction ("output") or to the prediction and every
+member of both instants of the forecast ensemble ("in_loop").
 """
 
 from __future__ import annotations
@@ -34,6 +37,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import philox
+from . import piston as _piston
 from .fried import fried_matrix
 from .geometry import Domain, Geometry
 
@@ -105,8 +109,13 @@ class OracleFilter:
     def __init__(self, geom: Geometry, domains: Optional[List[Domain]], m: int, a: float,
                  sigma: float, seed: int, L: Optional[np.ndarray] = None, q_white: float = 0.0,
                  obs_block: int = 1, X0: Optional[np.ndarray] = None,
-                 L_stat: Optional[np.ndarray] = None, a2: float = 0.0):
+                 L_stat: Optional[np.ndarray] = None, a2: float = 0.0, piston: str = "off"):
+        if piston not in ("off", "output", "in_loop"):
+            raise ValueError("piston must be 'off', 'output' or 'in_loop'")
+        if piston != "off" and domains is None:
+            raise ValueError("differential pistons exist only between domains")
         self.geom, self.domains, self.m, self.a = geom, domains, m, float(a)
+        self.piston = piston
         self.a2 = float(a2)
         self.sigma, self.seed, self.L, self.q_white = float(sigma), int(seed), L, float(q_white)
         self.L_stat = L_stat
@@ -156,7 +165,17 @@ class OracleFilter:
 
     def step(self, y: np.ndarray, sigma: Optional[float] = None,
              V: Optional[np.ndarray] = None) -> np.ndarray:
-        """Analysis with y_k, then forecast; returns x_hat(k+1|k) on the first block."""
+        """Analysis with y_k, then forecast; returns x_hat(k+1|k) on the first block (corrected
+        for differential pistons when that mode is on)."""
         self.analyze(y, sigma)
         self.forecast(V)
-        return self.X[: self.geom.n_act].mean(axis=1)
+        na = self.geom.n_act
+        xhat = self.X[:na].mean(axis=1)
+        if self.piston == "off":
+            return xhat
+        shift = _piston.ownership(self.geom, self.domains) @ _piston.differential_pistons(
+            xhat, y, self.geom, self.domains)
+        if self.piston == "in_loop":
+            self.X[:na] += shift[:, None]
+            self.X[na:] += shift[:, None]
+        return xhat + shift
