@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="fused path: default launch tuning")
     ap.add_argument("--mix-seconds", type=float, default=2.0, help="arrival window of the serving mix")
     ap.add_argument("--ns-frames", type=int, default=10000, help="frames of the non-stationary serving run")
+    ap.add_argument("--no-piston", action="store_true", help="skip the differential-piston leg")
+    ap.add_argument("--piston-frames", type=int, default=600, help="frames of the differential-piston leg")
     return ap.parse_args()
 
 
@@ -132,11 +134,11 @@ def residual_rms(xpred, phi, burn):
     return float(math.sqrt(np.mean(np.sum(e * e, axis=1) / e.shape[1])))
 
 
-def make_filter(w, path, precision, L, Ls, seed_offset=0):
+def make_filter(w, path, precision, L, Ls, seed_offset=0, piston="off"):
     from paper_1310_5954_gb300 import LETKF
     return LETKF(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
                  obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=precision, path=path,
-                 seed=w.seed + seed_offset, obs_block=w.obs_block)
+                 seed=w.seed + seed_offset, obs_block=w.obs_block, piston=piston)
 
 
 def run_device(f, y_dev, K, W, flush, torch):
@@ -260,20 +262,49 @@ def roofline(f, prof, sms, sm_max_mhz):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
 
 
-def cpu_baseline(wname, y, seconds, L, Ls):
+def cpu_baseline(wname, y, seconds, L, Ls, piston="off"):
     """The FP64 oracle as it stands, on this host's cores, over the first frames of the workload."""
     from oracle import etkf, geometry
     from synth import workload
     w = workload(wname)
     g = geometry.make_geometry(w.n_sub, w.obstruction)
     doms = geometry.make_domains(g, w.dom_sub, w.halo)
-    o = etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls)
+    o = etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls, piston=piston)
     preds = []
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds and len(preds) < len(y):
         preds.append(o.step(y[len(preds)]))
     dt = time.perf_counter() - t0
     return len(preds) / dt, np.array(preds), len(preds), dt
+
+
+def piston_leg(w, path, precision, L, Ls, y, phi, n_frames, flush, tuning, torch):
+    """Differential pistons between domains (Sect. 3.1, Sect. 5): the same frames through the filter
+    without correction, with the output corrected, and with the correction in the loop; per mode the
+    per-step time (CUDA events, L2 flushed before each step), the residual RMS after a burn-in of
+    half the frames, and the two correction kernels' share of the step."""
+    n = min(n_frames, len(y))
+    burn = n // 2
+    out = {"frames": n, "burn_in": burn, "modes": {}}
+    preds_in_loop = None
+    for mode in ("off", "output", "in_loop"):
+        f = make_filter(w, path, precision, L, Ls, 0, piston=mode)
+        if path == "fused" and tuning:
+            f.set_tuning(**tuning)
+        ydev = torch.as_tensor(y[:n], dtype=f.dtype, device=f.device).contiguous()
+        ms, preds, _ = run_device(f, ydev, n - 3, 3, flush, torch)
+        rec = {"frames_per_s": (n - 3) / (sum(ms) / 1e3), "p50_ms": float(np.percentile(ms, 50)),
+               "p99_ms": float(np.percentile(ms, 99)), "residual_rms": residual_rms(preds, phi, burn)}
+        if mode != "off":
+            prof = stage_profile(f, ydev, 30, flush, torch)
+            if "differential_pistons" in prof:
+                rec["piston_kernels_ms_per_step"] = prof["differential_pistons"][0] / 30
+        rec["device_status"] = f.sync()
+        f.close()
+        out["modes"][mode] = rec
+        if mode == "in_loop":
+            preds_in_loop = preds
+    return out, preds_in_loop
 
 
 def _geometry(w):
@@ -558,6 +589,10 @@ def main():
             out["residual_rms"]["plain"] = residual_rms(predp, phi, burn)
             out["speedup_vs_plain"] = out["value"] / out["plain"]["value"]
             fp.close()
+    preds_pl = None
+    if rank == 0 and world == 1 and not args.no_piston:
+        out["piston_removal"], preds_pl = piston_leg(w, args.path, precision, L, Ls, y, phi, args.piston_frames,
+                                                     flush, tuned.get(args.path, {}).get("tuning"), torch)
     ns_inputs = None
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving_mix"] = serving_mix_leg(args.mix_seconds)
@@ -572,6 +607,13 @@ def main():
                                                       args.path: residual_rms(preds[:nfr], phi, nb)}
         if "plain" in out:
             out["residual_rms"]["oracle_first_frames"]["plain"] = residual_rms(predp[:nfr], phi, nb)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and preds_pl is not None:
+        # the oracle's in-loop filter on the first frames, next to the GPU's in-loop run
+        _, opl, nfr, dt = cpu_baseline(args.workload, y, args.cpu_seconds / 2, L, Ls, piston="in_loop")
+        nb = min(burn, max(nfr - 2, 0))
+        out["piston_removal"]["oracle_first_frames"] = {"frames": nfr, "burn_in": nb, "seconds": dt,
+                                                        "oracle_in_loop": residual_rms(opl, phi, nb),
+                                                        "gpu_in_loop": residual_rms(preds_pl[:nfr], phi, nb)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and ns_inputs is not None:
         out["serving_nonstationary"]["oracle_first_frames"] = cpu_baseline_nonstationary(ns_inputs, 15.0)
     if rank == 0:

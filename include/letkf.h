@@ -74,6 +74,21 @@ typedef enum letkf_path {
     LETKF_PATH_FUSED = 1    /* one persistent kernel per frame over all domains */
 } letkf_path;
 
+/* Differential pistons between domains (Sect. 3.1, discussion of Fig. 3; Sect. 5).  The domains
+ * are analysed independently, so the stitched estimate carries one piston error per domain.  After
+ * each frame one piston per domain is fitted by least squares to the slope residual y_k - D x_hat of
+ * the prediction, on the subapertures whose corners lie in more than one domain, with the free
+ * constant of each connected group of domains chosen so that the correction adds no piston; the
+ * prediction returned is x_hat plus each actuator's domain piston.  The operator is formed on the
+ * host at create time (FP64 Cholesky of the domains' normal matrix, n_dom^2 elements on the
+ * device).  A rejected frame (non-finite slopes) is returned uncorrected. */
+typedef enum {
+    LETKF_PISTON_OFF = 0,       /* no correction */
+    LETKF_PISTON_OUTPUT = 1,    /* correct the returned prediction only (post-processing) */
+    LETKF_PISTON_IN_LOOP = 2    /* also shift every member of both instants of each domain's
+                                   owned actuators, so the next analysis starts corrected */
+} letkf_piston;
+
 typedef struct letkf_params {
     int n_sub;                      /* N: subapertures across; (N+1)^2 actuator grid (Fried) */
     const unsigned char* sub_valid; /* host N*N row-major validity mask, or NULL: circular pupil
@@ -104,6 +119,8 @@ typedef struct letkf_params {
                                        AR 2"): A1 = [[a I, a2 I], [I, 0]]; 0 is the AR(1) model.
                                        The AR(2) must be stationary: |a2| < 1, a + a2 < 1,
                                        a2 - a < 1 (for a2 = 0: |a| < 1) */
+    int piston;                     /* letkf_piston: differential-piston removal between domains
+                                       (letkf_step and the server only) */
 } letkf_params;
 
 typedef struct letkf_info {
@@ -156,6 +173,16 @@ typedef struct letkf_domain_sizes {
 
 int letkf_domain_tables(const letkf_params* params, letkf_domain_sizes* sizes, int* own_off, int* own,
                         int* obs_off, int* obs_sub, int* halo_off, int* halo, int* block);
+
+/*
+ * letkf_piston_operator: the least-squares operator of the differential-piston removal
+ * (letkf_piston) for these parameters, on the host (no GPU): *n_dom is set first; K, if not
+ * NULL, receives n_dom * n_dom doubles, row-major, with delta = K g where
+ * g_l = sum over boundary rows r of (D P)[r, l] (y - D x_hat)[r] (domain numbering as in
+ * letkf_domain_tables).  K = Pi M^+ with M = (D P)^T (D P) and Pi the projection that makes each
+ * connected group's correction add no piston.  LETKF_EINVAL for parameters letkf_create rejects.
+ */
+int letkf_piston_operator(const letkf_params* params, double* K, int* n_dom);
 
 /* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
 int letkf_destroy(letkf_ctx* ctx);
@@ -266,13 +293,13 @@ const char* letkf_status_string(int status);
  * Stage timing (instrumentation; the paper has no counterpart).  Stages:
  * 0 slope check, 1 process-noise draw (normals + GEMM), 2 observed anomalies,
  * 3 Gram, 4 eigensolve and weights, 5 transform, 6 forecast, 7 fused
- * analysis+forecast.  letkf_profile(ctx, 1, NULL) starts recording a pair of
+ * analysis+forecast, 8 differential pistons (each of its two kernels is one record).  letkf_profile(ctx, 1, NULL) starts recording a pair of
  * CUDA events around every stage launched on the context's stream (previous
  * records are dropped); letkf_profile(ctx, 0, out) stops, waits for the recorded
  * work and writes, per stage, the summed event time in milliseconds and the
  * number of launches.  Recording adds two event records per launch.
  */
-#define LETKF_N_STAGES 8
+#define LETKF_N_STAGES 9
 typedef struct letkf_stage_times {
     double ms[LETKF_N_STAGES];
     int launches[LETKF_N_STAGES];

@@ -19,6 +19,7 @@ LETKF_ETIMEOUT, LETKF_ENONFINITE, LETKF_ESTATE, LETKF_ENOCONV = -4, -5, -6, -7
 LETKF_ESCRATCH, LETKF_EBUSY = -8, -9
 LETKF_PREC_FP64, LETKF_PREC_FP32, LETKF_PREC_MIXED = 0, 1, 2
 LETKF_PATH_PLAIN, LETKF_PATH_FUSED = 0, 1
+LETKF_PISTON_OFF, LETKF_PISTON_OUTPUT, LETKF_PISTON_IN_LOOP = 0, 1, 2
 
 
 class letkf_params(ctypes.Structure):
@@ -41,6 +42,7 @@ class letkf_params(ctypes.Structure):
         ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("ar2_a", ctypes.c_double),
+        ("piston", ctypes.c_int),
     ]
 
 
@@ -83,7 +85,7 @@ class letkf_tuning(ctypes.Structure):
     _fields_ = [("fused_grid", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
-N_STAGES = 8
+N_STAGES = 9
 
 
 class letkf_stage_times(ctypes.Structure):
@@ -114,6 +116,7 @@ _SIGS = {
     "letkf_domain_tables": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(letkf_domain_sizes),
                                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "letkf_piston_operator": (ctypes.c_int, [ctypes.POINTER(letkf_params), _VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
     "letkf_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
     "letkf_autotune": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(letkf_tuning),
@@ -287,6 +290,17 @@ def letkf_domain_tables(params: letkf_params) -> dict:
            "letkf_domain_tables")
     out.update({f: getattr(sz, f) for f, _ in letkf_domain_sizes._fields_})
     return out
+
+
+def letkf_piston_operator(params: letkf_params):
+    """The differential-piston least-squares operator K (n_dom x n_dom float64) on the host."""
+    import numpy as np
+    nd = ctypes.c_int()
+    _check(load().letkf_piston_operator(ctypes.byref(params), None, ctypes.byref(nd)), "letkf_piston_operator")
+    K = np.zeros((nd.value, nd.value), np.float64)
+    _check(load().letkf_piston_operator(ctypes.byref(params), K.ctypes.data, ctypes.byref(nd)),
+           "letkf_piston_operator")
+    return K
 
 
 def letkf_footprint(params: letkf_params) -> int:

@@ -184,7 +184,7 @@ int alloc(letkf_ctx* c, void** p, size_t bytes) {
 }
 
 void free_all(letkf_ctx* c) {
-    void* ptrs[] = {c->X[0], c->X[1], c->Lq, c->Xi, c->Lt, c->noise_items, c->noise_tabs, c->noise_part, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
+    void* ptrs[] = {c->pst_ent, c->pst_off, c->pst_K, c->pst_g, c->xhat, c->X[0], c->X[1], c->Lq, c->Xi, c->Lt, c->noise_items, c->noise_tabs, c->noise_part, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
                     c->d_status, c->d_frame_bad, c->d_queue, c->tab.own_off, c->tab.own, c->tab.obs_off,
                     c->tab.obs_sub, c->tab.obs_corner, c->tab.halo_off, c->tab.halo, c->tab.order};
     for (void* p : ptrs)
@@ -213,7 +213,8 @@ int validate(const letkf_params* p) {
         !(p->sigma > 0) || !(std::fabs(p->ar2_a) < 1.0) || !(p->ar1_a + p->ar2_a < 1.0) ||
         !(p->ar2_a - p->ar1_a < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
         p->precision < 0 || p->precision > 2 || p->path < 0 || p->path > 1 || p->q_white < 0 ||
-        !(p->obstruction >= 0 && p->obstruction < 1))
+        !(p->obstruction >= 0 && p->obstruction < 1) || p->piston < LETKF_PISTON_OFF ||
+        p->piston > LETKF_PISTON_IN_LOOP)
         return LETKF_EINVAL;
     if (p->precision == LETKF_PREC_FP64 && p->path != LETKF_PATH_PLAIN) return LETKF_EINVAL;
     if (p->precision == LETKF_PREC_MIXED && p->path != LETKF_PATH_FUSED) return LETKF_EINVAL;
@@ -253,6 +254,7 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
     } else if (p->q_sqrt) {
         b += na * na * eb + na * row;
     }
+    if (p->piston != LETKF_PISTON_OFF) b += letkf::piston_bytes(h, (int)nd, (int)eb);
     return b;
 }
 
@@ -260,6 +262,7 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     if (validate(p)) return LETKF_EINVAL;
     c->n_sub = p->n_sub; c->m = p->m; c->dom_sub = p->dom_sub; c->halo = p->halo;
     c->precision = p->precision; c->path = p->path; c->obs_block = p->obs_block; c->device = p->device;
+    c->piston = p->piston;
     c->a = p->ar1_a; c->a2 = p->ar2_a; c->sigma = p->sigma; c->q_white = p->q_white; c->seed = p->seed;
     c->stream = (cudaStream_t)p->stream;
     const int eb = c->precision == LETKF_PREC_FP64 ? 8 : 4;
@@ -308,6 +311,7 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
         if ((rc = letkf::fused_prepare(c))) return rc;
     }
     if ((rc = letkf::init_ensemble(c, p->q_sqrt, p->p0_sqrt))) return rc;
+    if ((rc = letkf::piston_prepare(c))) return rc;
     CU(cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->phase = 0;
@@ -366,6 +370,22 @@ int letkf_footprint(const letkf_params* p, unsigned long long* bytes) {
     build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
     if (h.n_act == 0 || h.own_off.size() < 2) return LETKF_EINVAL;
     *bytes = footprint_bytes(p, h);
+    return LETKF_OK;
+}
+
+int letkf_piston_operator(const letkf_params* p, double* K, int* n_dom) {
+    if (!p || !n_dom) return LETKF_EINVAL;
+    if (validate(p)) return LETKF_EINVAL;
+    letkf::HostModel h;
+    build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    const int nd = (int)h.own_off.size() - 1;
+    if (h.n_act == 0 || nd < 1) return LETKF_EINVAL;
+    *n_dom = nd;
+    if (!K) return LETKF_OK;
+    std::vector<double> k;
+    const int rc = letkf::piston_operator_host(h, nd, &k);
+    if (rc) return rc;
+    std::memcpy(K, k.data(), k.size() * sizeof(double));
     return LETKF_OK;
 }
 
@@ -464,14 +484,18 @@ int letkf_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
     if (c->phase != 0) return LETKF_ESTATE;
     CU(cudaSetDevice(c->device));
     int rc;
+    // with differential-piston removal the kernels write the raw prediction to c->xhat and the
+    // corrected one goes to the caller's buffer
+    void* xp = c->piston != LETKF_PISTON_OFF ? c->xhat : xpred;
     if (c->path == LETKF_PATH_PLAIN) {
         if ((rc = letkf::plain_analyze(c, y, sigma))) return rc;
         c->cur ^= 1;
-        if ((rc = letkf::launch_forecast(c, nullptr, xpred, 1))) return rc;
+        if ((rc = letkf::launch_forecast(c, nullptr, xp, 1))) return rc;
     } else {
-        if ((rc = letkf::fused_step(c, y, sigma, xpred, 1))) return rc;
+        if ((rc = letkf::fused_step(c, y, sigma, xp, 1))) return rc;
         c->cur ^= 1;
     }
+    if ((rc = letkf::piston_launch(c, y, xpred, c->X[c->cur], c->stream))) return rc;
     c->phase = 0;
     c->frame += 1;
     return LETKF_OK;
@@ -564,7 +588,7 @@ int letkf_profile(letkf_ctx* c, int enable, letkf_stage_times* out) {
 const char* letkf_stage_name(int s) {
     static const char* names[LETKF_N_STAGES] = {"slope_check", "noise_draw", "observed_anomalies", "gram",
                                                "eigensolve_weights", "transform", "forecast",
-                                               "fused_analysis_forecast"};
+                                               "fused_analysis_forecast", "differential_pistons"};
     return (s >= 0 && s < LETKF_N_STAGES) ? names[s] : "unknown";
 }
 

@@ -116,6 +116,15 @@ struct letkf_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t cap_stream = nullptr;      // capture only
     cublasHandle_t cublas_cap = nullptr;
+    // differential-piston removal: per-domain entries of the boundary subapertures, the
+    // least-squares operator K (n_dom x n_dom), per-domain residual sums and the raw prediction
+    int piston = 0;
+    void* pst_ent = nullptr;
+    int* pst_off = nullptr;
+    int pst_n_ent = 0;
+    void* pst_K = nullptr;
+    void* pst_g = nullptr;
+    void* xhat = nullptr;
     // stage timing
     int prof_on = 0;
     std::vector<int> prof_stage;            // stage of each record
@@ -128,7 +137,7 @@ namespace letkf {
 int state_bytes(const letkf_ctx* c);
 
 enum Stage { STAGE_CHECK = 0, STAGE_NOISE = 1, STAGE_OBS = 2, STAGE_GRAM = 3, STAGE_EIG = 4,
-             STAGE_TRANSFORM = 5, STAGE_FORECAST = 6, STAGE_FUSED = 7 };
+             STAGE_TRANSFORM = 5, STAGE_FORECAST = 6, STAGE_FUSED = 7, STAGE_PISTON = 8 };
 // Record the start / end of a stage on the context's stream (no-ops unless profiling).
 void prof_begin(letkf_ctx* c, int stage);
 void prof_end(letkf_ctx* c);
@@ -156,6 +165,15 @@ struct NormalsNode {
     uint32_t stream_id, frame;
 };
 int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
+
+// piston.cu: differential pistons between domains
+size_t piston_bytes(const HostModel& h, int n_dom, int elem_bytes);
+// The least-squares operator K (n_dom x n_dom, FP64, row-major), on the host.
+int piston_operator_host(const HostModel& h, int n_dom, std::vector<double>* K);
+int piston_prepare(letkf_ctx* c);
+// After a frame whose prediction is in c->xhat: x_out = x_hat + P delta (x_out may be null) and,
+// in the in-loop mode, the shift of the new state X (both instants).
+int piston_launch(letkf_ctx* c, const void* y, void* xout, void* X, cudaStream_t stream);
 
 // noise.cu: the mixed-precision draw V = L Xi on the tensor cores
 struct NoisePlan {

@@ -326,7 +326,11 @@ int noise_prepare(letkf_ctx* c, const double* L) {
     c->noise_n_items = P.n_items;
     c->noise_n_rb = n_rb;
     const int smem = noise_smem(P.np);
-    if (cudaFuncSetAttribute(noise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    // the attribute belongs to the kernel, not to this context: it is set to what the widest
+    // ensemble (m = 256) needs, so that a context created later with a smaller m cannot lower it
+    // below what an earlier context's launches use
+    if (cudaFuncSetAttribute(noise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, noise_smem(256)) !=
+        cudaSuccess)
         return LETKF_ECUDA;
     if (cudaFuncSetAttribute(noise_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess)

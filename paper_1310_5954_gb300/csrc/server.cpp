@@ -150,13 +150,15 @@ int launch(letkf_server* S) {
         if (cudaMemcpyAsync(s.y_dev, s.y_pinned + (size_t)w.buf * s.p, (size_t)s.p * 4, cudaMemcpyHostToDevice,
                             sl.stream) != cudaSuccess)
             return LETKF_ECUDA;
-        frames.push_back({s.c, s.y_dev, w.sigma, s.xpred_dev, 1});
+        frames.push_back({s.c, s.y_dev, w.sigma, s.c->piston != LETKF_PISTON_OFF ? s.c->xhat : s.xpred_dev, 1});
     }
     sl.t_launch = now_ns();
     int rc = letkf::fused_batch(frames.data(), (int)frames.size(), sl.queue, sl.stream);
     if (rc) return rc;
     for (int id : ready) {
         System& s = S->sys[id];
+        // differential pistons: the new state is the context's other buffer until the swap below
+        if ((rc = letkf::piston_launch(s.c, s.y_dev, s.xpred_dev, s.c->X[s.c->cur ^ 1], sl.stream))) return rc;
         if (cudaMemcpyAsync(s.pred_pinned, s.xpred_dev, (size_t)s.n_act * 4, cudaMemcpyDeviceToHost, sl.stream) !=
                 cudaSuccess ||
             cudaMemcpyAsync(s.bad_pinned, s.c->d_frame_bad, sizeof(int), cudaMemcpyDeviceToHost, sl.stream) !=

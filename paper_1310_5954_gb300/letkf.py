@@ -18,13 +18,14 @@ from . import _lib
 
 _PREC = {"fp64": _lib.LETKF_PREC_FP64, "fp32": _lib.LETKF_PREC_FP32, "mixed": _lib.LETKF_PREC_MIXED}
 _PATH = {"plain": _lib.LETKF_PATH_PLAIN, "fused": _lib.LETKF_PATH_FUSED}
+_PISTON = {"off": _lib.LETKF_PISTON_OFF, "output": _lib.LETKF_PISTON_OUTPUT, "in_loop": _lib.LETKF_PISTON_IN_LOOP}
 
 
 def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4, halo: int = 2,
                 obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
                 q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0, p0_sqrt: Optional[np.ndarray] = None,
                 precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1,
-                ar2_a: float = 0.0):
+                ar2_a: float = 0.0, piston: str = "off"):
     """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used)."""
     p = _lib.letkf_params()
     keep = []
@@ -53,6 +54,9 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
     p.path = _PATH[path]
     p.seed = int(seed)
     p.ar2_a = float(ar2_a)
+    if piston not in _PISTON:
+        raise ValueError(f"piston must be one of {sorted(_PISTON)}")
+    p.piston = _PISTON[piston]
     return p, keep
 
 
@@ -70,7 +74,7 @@ class LETKF:
                  q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0,
                  p0_sqrt: Optional[np.ndarray] = None, precision: str = "fp32", path: str = "plain",
                  seed: int = 0, obs_block: int = 1, device: Optional[int] = None, stream=None,
-                 ar2_a: float = 0.0):
+                 ar2_a: float = 0.0, piston: str = "off"):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -81,7 +85,7 @@ class LETKF:
         p, keep = make_params(n_sub=n_sub, m=m, ar1_a=ar1_a, sigma=sigma, dom_sub=dom_sub, halo=halo,
                               obstruction=obstruction, sub_valid=sub_valid, q_sqrt=q_sqrt, q_white=q_white,
                               p0_sqrt=p0_sqrt, precision=precision, path=path, seed=seed, obs_block=obs_block,
-                              ar2_a=ar2_a)
+                              ar2_a=ar2_a, piston=piston)
         self._keep = keep
         p.device = dev
         p.stream = self.stream.cuda_stream
@@ -92,6 +96,7 @@ class LETKF:
         self.noise_kind = "dense" if q_sqrt is not None else ("white" if q_white > 0 else "none")
         self.dtype = torch.float64 if self.info.state_bytes == 8 else torch.float32
         self.precision, self.path = precision, path
+        self.piston = piston
 
     # --- geometry -------------------------------------------------------------------
     def geometry(self):

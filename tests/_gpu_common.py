@@ -35,18 +35,18 @@ def slopes(name, n_frames, **over):
     return np.ascontiguousarray(y), np.ascontiguousarray(fr["phi_act"][:, g.act_valid])
 
 
-def oracle_filter(name, m=None, **over):
+def oracle_filter(name, m=None, piston="off", **over):
     w, g, doms, L, Ls = model(name, m, **over)
     return etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls, obs_block=w.obs_block,
-                             a2=w.ar2_a)
+                             a2=w.ar2_a, piston=piston)
 
 
-def gpu_filter(name, precision, path, m=None, **over):
+def gpu_filter(name, precision, path, m=None, piston="off", **over):
     from paper_1310_5954_gb300 import LETKF
     w, g, doms, L, Ls = model(name, m, **over)
     return LETKF(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
                  obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=precision, path=path,
-                 seed=w.seed, obs_block=w.obs_block, ar2_a=w.ar2_a)
+                 seed=w.seed, obs_block=w.obs_block, ar2_a=w.ar2_a, piston=piston)
 
 
 def rel(a, b):

@@ -49,7 +49,8 @@ def _params(**kw):
                                  dict(path=3), dict(obstruction=1.5), dict(q_white=-1.0),
                                  dict(precision=_lib.LETKF_PREC_FP64, path=_lib.LETKF_PATH_FUSED),
                                  dict(precision=_lib.LETKF_PREC_MIXED, path=_lib.LETKF_PATH_PLAIN),
-                                 dict(precision=_lib.LETKF_PREC_FP64, m=200), dict(dom_sub=12, halo=2)])
+                                 dict(precision=_lib.LETKF_PREC_FP64, m=200), dict(dom_sub=12, halo=2),
+                                 dict(piston=3), dict(piston=-1)])
 def test_create_rejects_invalid_parameters_before_touching_the_device(lib, bad):
     p = _params(**bad)
     out = ctypes.c_void_p(1234)
