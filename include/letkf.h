@@ -184,6 +184,15 @@ int letkf_domain_tables(const letkf_params* params, letkf_domain_sizes* sizes, i
  */
 int letkf_piston_operator(const letkf_params* params, double* K, int* n_dom);
 
+/*
+ * letkf_gemm_selftest (tests): C (M x N, row-major) = A (M x K) B (N x K)^T with A, B FP32 row-major
+ * device arrays, through the library's tiled tensor-core GEMM (BF16 operands; split = 1 adds the
+ * two low-part products, ~2^-16 relative per element; bn = 64 or 128 columns per CTA tile).
+ * Ordered on `stream` and synchronised.  LETKF_ETIMEOUT if a bounded wait inside gave up.
+ */
+int letkf_gemm_selftest(const float* A, const float* B, float* C, int M, int N, int K, int split, int bn,
+                        void* stream);
+
 /* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
 int letkf_destroy(letkf_ctx* ctx);
 

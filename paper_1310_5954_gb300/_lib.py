@@ -112,6 +112,8 @@ _SIGS = {
                                            _VP]),
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
     "letkf_wait_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _VP]),
+    "letkf_gemm_selftest": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, _VP]),
     "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
     "letkf_domain_tables": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(letkf_domain_sizes),
                                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),

@@ -166,6 +166,40 @@ struct NormalsNode {
 };
 int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
 
+// gemm.cu: tiled tensor-core GEMM, C = A B^T with tiled BF16 operands (128 x 64 tiles)
+enum GemmEpilogue { GEMM_EPI_F32 = 0, GEMM_EPI_TILES = 1, GEMM_EPI_ADD_ROW = 2 };
+struct GemmArgs {
+    const uint8_t* a_hi;
+    const uint8_t* a_lo;        // null: single BF16
+    const uint8_t* b_hi;
+    const uint8_t* b_lo;
+    int a_nkb, b_nkb;           // column tiles per row tile of A and B
+    int nkb;                    // K / 64 steps to run
+    int split;                  // 1: hi hi + hi lo + lo hi
+    int M, N;                   // valid rows / columns of C
+    int mode;                   // GemmEpilogue
+    float* c;                   // F32 / ADD_ROW: C[row * ldc + col]
+    int ldc;
+    float alpha;
+    uint8_t* o_hi;              // TILES: alpha C + beta I as a tiled operand with o_nkb column tiles
+    uint8_t* o_lo;
+    int o_nkb;
+    float beta;
+    unsigned int* dev;          // TILES: max |C - I| over valid entries (float bits, atomicMax)
+    const float* add;           // ADD_ROW: per-row term
+    const int* run;             // non-null: the launch does nothing when *run == 0
+    int* run_next;              // non-null: CTA (0,0) sets *run_next = (*run_dev >= run_tol)
+    const unsigned int* run_dev;
+    float run_tol;
+    int* z_final;               // non-null: CTA (0,0) sets *z_final = z_index
+    int z_index;
+    int* status;
+};
+size_t tiled_bytes(int rows, int cols);
+int gemm_prepare();
+int gemm_launch(const GemmArgs& g, int bn, int m_tiles, int n_tiles, cudaStream_t stream);
+int to_tiles(const float* src, int R, int K, int ld, void* hi, void* lo, cudaStream_t stream);
+
 // piston.cu: differential pistons between domains
 size_t piston_bytes(const HostModel& h, int n_dom, int elem_bytes);
 // The least-squares operator K (n_dom x n_dom, FP64, row-major), on the host.
