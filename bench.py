@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--mix-seconds", type=float, default=2.0, help="arrival window of the serving mix")
     ap.add_argument("--ns-frames", type=int, default=10000, help="frames of the non-stationary serving run")
     ap.add_argument("--no-piston", action="store_true", help="skip the differential-piston leg")
+    ap.add_argument("--no-global", action="store_true", help="skip the global-ETKF (m = 1024) leg")
+    ap.add_argument("--global-steps", type=int, default=200, help="timed steps of the global-ETKF leg")
     ap.add_argument("--piston-frames", type=int, default=600, help="frames of the differential-piston leg")
     return ap.parse_args()
 
@@ -307,10 +309,52 @@ def piston_leg(w, path, precision, L, Ls, y, phi, n_frames, flush, tuning, torch
     return out, preds_in_loop
 
 
+def global_leg(steps, warmup, flush, torch, workers=16):
+    """Global ETKF (Sect. 2.2: one domain, the whole pupil) at ELT scale with 1024 members on the
+    tiled tensor-core GEMM: per-step time (CUDA events, L2 flushed before each step), the stage
+    times, the algorithmic FP32 work per frame (Gram, Newton-Schulz products, transform, noise
+    draw) and its rate; the tensor-core work is three split-BF16 products per FP32 product."""
+    from paper_1310_5954_gb300 import LETKF
+    from synth import compressed_frames, workload
+    w = workload("etkf-elt-m1024")
+    sv, av = _geometry(w)
+    act_rc = np.argwhere(av)
+    L = w.process_noise_sqrt(act_rc)
+    Ls = w.stationary_sqrt(act_rc)
+    n_fr = warmup + steps
+    y, phi, _ = compressed_frames(w, 0, n_fr + 1, sv, av, workers)
+    f = LETKF(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls,
+              precision="fp32", path="global", seed=w.seed, obs_block=w.obs_block)
+    ydev = torch.as_tensor(y[:n_fr], dtype=torch.float32, device=f.device).contiguous()
+    ms, preds, _ = run_device(f, ydev, steps, warmup, flush, torch)
+    ns_steps, s_bound = f.global_stats()
+    prof = stage_profile(f, ydev, 20, flush, torch)
+    status = f.sync()
+    m, n, p, na = f.info.m, f.info.n, f.info.p, f.info.n_act
+    lower = bool(np.allclose(L, np.tril(L)))
+    work = {"gram": 2.0 * (m + 1) ** 2 * p, "newton_schulz": 2.0 * m ** 3 * (1 + 3 * max(ns_steps - 1, 0)),
+            "transform": 2.0 * n * m * m, "noise": 2.0 * na * na * m / (2.0 if lower else 1.0)}
+    tot = sum(work.values())
+    t_med = float(np.median(ms)) / 1e3
+    f.close()
+    burn = n_fr // 2
+    return {"workload": f"{w.name}: 80x80, 28% obstruction, one domain (n={n}, p={p}), m={m}, FP32 "
+                        f"(split-BF16 tensor-core products)",
+            "frames_per_s": steps / (sum(ms) / 1e3), "p50_ms": float(np.median(ms)), "p99_ms": float(np.percentile(ms, 99)),
+            "stages_ms_per_step": {k: v[0] / 20 for k, v in prof.items()},
+            "newton_schulz_steps_last_frame": ns_steps, "spectral_bound_last_frame": s_bound,
+            "fp32_work_gflop_per_frame": {k: v / 1e9 for k, v in work.items()},
+            "fp32_work_tflops_at_p50": tot / t_med / 1e12,
+            "bf16_tensor_tflops_at_p50": 3.0 * tot / t_med / 1e12,
+            "residual_rms": {"frames": n_fr, "burn_in": burn, "gpu": residual_rms(preds, phi, burn)},
+            "device_status": status}
+
+
 def _geometry(w):
     """Valid subaperture / actuator masks as the library computes them (a small probe context)."""
     from paper_1310_5954_gb300 import LETKF
-    probe = LETKF(n_sub=w.n_sub, m=4, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
+    # the masks do not depend on the domains: any valid decomposition serves
+    probe = LETKF(n_sub=w.n_sub, m=4, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=4, halo=0,
                   obstruction=w.obstruction, q_white=0.1, precision="fp32", path="plain")
     sv, av = probe.geometry()
     probe.close()
@@ -593,6 +637,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_piston:
         out["piston_removal"], preds_pl = piston_leg(w, args.path, precision, L, Ls, y, phi, args.piston_frames,
                                                      flush, tuned.get(args.path, {}).get("tuning"), torch)
+    if rank == 0 and world == 1 and not args.no_global:
+        out["global_etkf"] = global_leg(args.global_steps, 5, flush, torch)
     ns_inputs = None
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving_mix"] = serving_mix_leg(args.mix_seconds)

@@ -71,7 +71,11 @@ typedef enum letkf_precision {
 
 typedef enum letkf_path {
     LETKF_PATH_PLAIN = 0,   /* one kernel per stage, one CTA per domain */
-    LETKF_PATH_FUSED = 1    /* one persistent kernel per frame over all domains */
+    LETKF_PATH_FUSED = 1,   /* one persistent kernel per frame over all domains */
+    LETKF_PATH_GLOBAL = 2   /* global ETKF (Sect. 2.2): one domain, the whole pupil, for large
+                               ensembles (2 <= m <= 4096, FP32 only): the Gram, the Newton-Schulz
+                               inverse square root, the transform and the process-noise draw as
+                               split-BF16 tensor-core products; dom_sub and halo are ignored */
 } letkf_path;
 
 /* Differential pistons between domains (Sect. 3.1, discussion of Fig. 3; Sect. 5).  The domains
@@ -187,11 +191,20 @@ int letkf_piston_operator(const letkf_params* params, double* K, int* n_dom);
 /*
  * letkf_gemm_selftest (tests): C (M x N, row-major) = A (M x K) B (N x K)^T with A, B FP32 row-major
  * device arrays, through the library's tiled tensor-core GEMM (BF16 operands; split = 1 adds the
- * two low-part products, ~2^-16 relative per element; bn = 64 or 128 columns per CTA tile).
+ * two low-part products, ~2^-16 relative per element; bn = 64 or 128 columns per CTA tile).  With
+ * b_mn = 1 (bn = 64 only) B is given as K x N row-major and C = A B, the tiles of B read MN-major.
  * Ordered on `stream` and synchronised.  LETKF_ETIMEOUT if a bounded wait inside gave up.
  */
 int letkf_gemm_selftest(const float* A, const float* B, float* C, int M, int N, int K, int split, int bn,
-                        void* stream);
+                        int b_mn, void* stream);
+
+/*
+ * letkf_global_stats (LETKF_PATH_GLOBAL): Newton-Schulz steps taken by the last analysis (the
+ * first, product-free step included; each further step is three products) and the spectral bound
+ * s = 1 + ||G||_F / (m-1) the iteration was scaled by.  Synchronises the context's stream;
+ * LETKF_ESTATE on other paths.
+ */
+int letkf_global_stats(letkf_ctx* ctx, int* ns_steps, double* s_bound);
 
 /* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
 int letkf_destroy(letkf_ctx* ctx);

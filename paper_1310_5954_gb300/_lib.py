@@ -18,7 +18,7 @@ LETKF_OK, LETKF_EINVAL, LETKF_ENOMEM, LETKF_ECUDA = 0, -1, -2, -3
 LETKF_ETIMEOUT, LETKF_ENONFINITE, LETKF_ESTATE, LETKF_ENOCONV = -4, -5, -6, -7
 LETKF_ESCRATCH, LETKF_EBUSY = -8, -9
 LETKF_PREC_FP64, LETKF_PREC_FP32, LETKF_PREC_MIXED = 0, 1, 2
-LETKF_PATH_PLAIN, LETKF_PATH_FUSED = 0, 1
+LETKF_PATH_PLAIN, LETKF_PATH_FUSED, LETKF_PATH_GLOBAL = 0, 1, 2
 LETKF_PISTON_OFF, LETKF_PISTON_OUTPUT, LETKF_PISTON_IN_LOOP = 0, 1, 2
 
 
@@ -113,11 +113,12 @@ _SIGS = {
     "letkf_footprint": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_ulonglong)]),
     "letkf_wait_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _VP]),
     "letkf_gemm_selftest": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                           ctypes.c_int, _VP]),
+                                           ctypes.c_int, ctypes.c_int, _VP]),
     "letkf_set_graph": (ctypes.c_int, [_VP, ctypes.c_int]),
     "letkf_domain_tables": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(letkf_domain_sizes),
                                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "letkf_global_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "letkf_piston_operator": (ctypes.c_int, [ctypes.POINTER(letkf_params), _VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
     "letkf_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
@@ -303,6 +304,14 @@ def letkf_piston_operator(params: letkf_params):
     _check(load().letkf_piston_operator(ctypes.byref(params), K.ctypes.data, ctypes.byref(nd)),
            "letkf_piston_operator")
     return K
+
+
+def letkf_global_stats(ctx: int):
+    """(Newton-Schulz steps, spectral bound s) of the last global-path analysis."""
+    n = ctypes.c_int()
+    sb = ctypes.c_double()
+    _check(load().letkf_global_stats(ctx, ctypes.byref(n), ctypes.byref(sb)), "letkf_global_stats")
+    return n.value, sb.value
 
 
 def letkf_footprint(params: letkf_params) -> int:

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libletkf.so")
-SOURCES = ["host.cpp", "plain.cu", "misc.cu", "fused.cu", "noise.cu", "piston.cu", "gemm.cu", "server.cpp", "tune.cpp"]
+SOURCES = ["host.cpp", "plain.cu", "misc.cu", "fused.cu", "noise.cu", "piston.cu", "gemm.cu", "global.cu", "server.cpp", "tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

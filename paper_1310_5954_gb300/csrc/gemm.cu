@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
         if (g.z_final) *g.z_final = g.z_index;
     }
     const int row0 = blockIdx.y * 128, col0 = blockIdx.x * BN;
-    const int nkb = g.nkb;
+    // a lower-triangular A has no nonzero column beyond its rows
+    const int nkb = g.a_lower ? min(g.nkb, 2 * ((int)blockIdx.y + 1)) : g.nkb;
     const bool split = g.split != 0;
     const uint32_t stage_bytes = split ? L::STAGE_SPLIT : L::STAGE_SPLIT / 2;
     if (tid == 0) {
@@ -91,8 +92,11 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
     // operand bases of this tile
     const uint8_t* a_hi = g.a_hi + (size_t)blockIdx.y * g.a_nkb * TILE_B;
     const uint8_t* a_lo = g.a_lo ? g.a_lo + (size_t)blockIdx.y * g.a_nkb * TILE_B : nullptr;
-    const size_t b_row_tile = (size_t)(col0 >> 7) * g.b_nkb * TILE_B;
-    const size_t b_half = (BN == 64 && (col0 & 64)) ? (size_t)L::B_BYTES : 0;
+    // B K-major (rows = N): the 128-row tile holding this CTA's columns, and its half for BN = 64.
+    // B MN-major (the second factor M itself, rows = K; BN = 64): the step-kb chunk is rows
+    // 64 kb .. 64 kb + 63 of column tile col0 / 64, the first or second half of that tile.
+    const size_t b_row_tile = g.b_mn ? (size_t)(col0 >> 6) * TILE_B : (size_t)(col0 >> 7) * g.b_nkb * TILE_B;
+    const size_t b_half = (!g.b_mn && BN == 64 && (col0 & 64)) ? (size_t)L::B_BYTES : 0;
     const uint8_t* b_hi = g.b_hi + b_row_tile + b_half;
     const uint8_t* b_lo = g.b_lo ? g.b_lo + b_row_tile + b_half : nullptr;
     int issued = 0;   // stages the producer filled (for the drain on abort)
@@ -106,17 +110,23 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
             }
             if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
             uint8_t* st = smem + (size_t)s * L::STAGE_SPLIT;
+            const size_t boff = g.b_mn ? ((size_t)(kb >> 1) * g.b_nkb) * TILE_B + (size_t)(kb & 1) * L::B_BYTES
+                                       : (size_t)kb * TILE_B;
             mbar_arrive_expect_tx(&full[s], stage_bytes);
             bulk_g2s(st, a_hi + (size_t)kb * TILE_B, TILE_B, &full[s]);
-            bulk_g2s(st + 2 * TILE_B, b_hi + (size_t)kb * TILE_B, L::B_BYTES, &full[s]);
+            bulk_g2s(st + 2 * TILE_B, b_hi + boff, L::B_BYTES, &full[s]);
             if (split) {
                 bulk_g2s(st + TILE_B, a_lo + (size_t)kb * TILE_B, TILE_B, &full[s]);
-                bulk_g2s(st + 2 * TILE_B + L::B_BYTES, b_lo + (size_t)kb * TILE_B, L::B_BYTES, &full[s]);
+                bulk_g2s(st + 2 * TILE_B + L::B_BYTES, b_lo + boff, L::B_BYTES, &full[s]);
             }
             issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
-        const uint32_t idesc = idesc_bf16(128, BN);
+        const uint32_t idesc = idesc_bf16(128, BN, g.b_mn);
+        // K-major B: K-adjacent core matrices 128 B apart, row-adjacent 1024 B, a K step 256 B;
+        // MN-major B: N-adjacent core matrices 128 B apart, K-adjacent 1024 B, a K step 2048 B
+        const uint32_t b_lbo = g.b_mn ? 1024u : 128u, b_sbo = g.b_mn ? 128u : 1024u;
+        const uint32_t b_step = g.b_mn ? 2048u : 256u;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % L::STAGES;
             if (!mbar_wait_bounded(&full[s], (kb / L::STAGES) & 1, GEMM_WAIT)) {
@@ -131,10 +141,12 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                mma_bf16(tmem, sdesc(sa_hi + 256 * k, 128, 1024), sdesc(sb_hi + 256 * k, 128, 1024), idesc, acc);
+                const uint64_t bh = sdesc(sb_hi + b_step * k, b_lbo, b_sbo);
+                mma_bf16(tmem, sdesc(sa_hi + 256 * k, 128, 1024), bh, idesc, acc);
                 if (split) {
-                    mma_bf16(tmem, sdesc(sa_hi + 256 * k, 128, 1024), sdesc(sb_lo + 256 * k, 128, 1024), idesc, 1u);
-                    mma_bf16(tmem, sdesc(sa_lo + 256 * k, 128, 1024), sdesc(sb_hi + 256 * k, 128, 1024), idesc, 1u);
+                    mma_bf16(tmem, sdesc(sa_hi + 256 * k, 128, 1024), sdesc(sb_lo + b_step * k, b_lbo, b_sbo), idesc,
+                             1u);
+                    mma_bf16(tmem, sdesc(sa_lo + 256 * k, 128, 1024), bh, idesc, 1u);
                 }
             }
             mma_commit(&empty[s]);
@@ -243,6 +255,7 @@ int gemm_prepare() {
 }
 
 int gemm_launch(const GemmArgs& g, int bn, int m_tiles, int n_tiles, cudaStream_t stream) {
+    if (g.b_mn && bn != 64) return LETKF_EINVAL;
     if (bn == 64) {
         gemm_kernel<64><<<dim3(n_tiles, m_tiles), GT, GemmSmem<64>::BYTES, stream>>>(g);
     } else if (bn == 128) {
@@ -267,10 +280,10 @@ int to_tiles(const float* src, int R, int K, int ld, void* hi, void* lo, cudaStr
 // C (M x N, leading dimension N) = A (M x K) B (N x K)^T through the tiled tensor-core GEMM, for
 // tests: A and B are FP32 row-major device arrays, converted to tiled BF16 (split when split = 1).
 extern "C" int letkf_gemm_selftest(const float* A, const float* B, float* C, int M, int N, int K, int split, int bn,
-                                   void* stream) {
+                                   int b_mn, void* stream) {
     using namespace letkf;
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || M > 16384 || N > 16384 || K > 65536 ||
-        (split != 0 && split != 1) || (bn != 64 && bn != 128))
+        (split != 0 && split != 1) || (bn != 64 && bn != 128) || (b_mn != 0 && b_mn != 1) || (b_mn && bn != 64))
         return LETKF_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mp = (M + 127) / 128 * 128, kp = (K + 63) / 64 * 64;
@@ -278,7 +291,9 @@ extern "C" int letkf_gemm_selftest(const float* A, const float* B, float* C, int
     uint8_t *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
     int* st = nullptr;
     int rc = gemm_prepare();
-    const size_t ab = tiled_bytes(mp, kp), bb = tiled_bytes(np, kp);
+    // B as tiles of B (N x K) itself, or (b_mn) of B given as K x N, rows padded to 128
+    const size_t ab = tiled_bytes(mp, kp), bb = b_mn ? tiled_bytes((K + 127) / 128 * 128, (N + 63) / 64 * 64)
+                                                     : tiled_bytes(np, kp);
     if (!rc && (cudaMalloc(&ah, ab) != cudaSuccess || cudaMalloc(&al, ab) != cudaSuccess ||
                 cudaMalloc(&bh, bb) != cudaSuccess || cudaMalloc(&bl, bb) != cudaSuccess ||
                 cudaMalloc(&st, sizeof(int)) != cudaSuccess))
@@ -286,7 +301,7 @@ extern "C" int letkf_gemm_selftest(const float* A, const float* B, float* C, int
     if (!rc) {
         cudaMemsetAsync(st, 0, sizeof(int), s);
         rc = to_tiles(A, M, K, K, ah, al, s);
-        if (!rc) rc = to_tiles(B, N, K, K, bh, bl, s);
+        if (!rc) rc = b_mn ? to_tiles(B, K, N, N, bh, bl, s) : to_tiles(B, N, K, K, bh, bl, s);
     }
     if (!rc) {
         GemmArgs g{};
@@ -294,7 +309,9 @@ extern "C" int letkf_gemm_selftest(const float* A, const float* B, float* C, int
         g.a_lo = split ? al : nullptr;
         g.b_hi = bh;
         g.b_lo = split ? bl : nullptr;
-        g.a_nkb = g.b_nkb = g.nkb = kp / 64;
+        g.a_nkb = g.nkb = kp / 64;
+        g.b_nkb = b_mn ? (N + 63) / 64 : kp / 64;
+        g.b_mn = b_mn;
         g.split = split;
         g.M = M;
         g.N = N;

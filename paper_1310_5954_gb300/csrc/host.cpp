@@ -183,6 +183,14 @@ int alloc(letkf_ctx* c, void** p, size_t bytes) {
     return LETKF_OK;
 }
 
+// The geometry and domains of these parameters (the global path: one domain, no halo).
+void build_for(HostModel& h, const letkf_params* p) {
+    if (p->path == LETKF_PATH_GLOBAL)
+        build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->n_sub, 0);
+    else
+        build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+}
+
 void free_all(letkf_ctx* c) {
     void* ptrs[] = {c->pst_ent, c->pst_off, c->pst_K, c->pst_g, c->xhat, c->X[0], c->X[1], c->Lq, c->Xi, c->Lt, c->noise_items, c->noise_tabs, c->noise_part, c->V, c->S, c->dt, c->G, c->b, c->W, c->so_off,
                     c->d_status, c->d_frame_bad, c->d_queue, c->tab.own_off, c->tab.own, c->tab.obs_off,
@@ -199,6 +207,7 @@ void free_all(letkf_ctx* c) {
     if (c->Xi_side) cudaFree(c->Xi_side);
     if (c->scratch) cudaFree(c->scratch);
     letkf::fused_graph_reset(c);
+    letkf::global_free(c);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->cublas_cap) cublasDestroy(c->cublas_cap);
@@ -209,6 +218,15 @@ void free_all(letkf_ctx* c) {
 }
 
 int validate(const letkf_params* p) {
+    if (p->path == LETKF_PATH_GLOBAL) {
+        // one domain: the domain size and halo play no part
+        if (p->n_sub < 1 || p->n_sub > 1024 || p->m < 2 || p->m > 4096 || !(p->sigma > 0) ||
+            !(std::fabs(p->ar2_a) < 1.0) || !(p->ar1_a + p->ar2_a < 1.0) || !(p->ar2_a - p->ar1_a < 1.0) ||
+            (p->obs_block != 0 && p->obs_block != 1) || p->precision != LETKF_PREC_FP32 || p->q_white < 0 ||
+            !(p->obstruction >= 0 && p->obstruction < 1) || p->piston != LETKF_PISTON_OFF)
+            return LETKF_EINVAL;
+        return LETKF_OK;
+    }
     if (p->n_sub < 1 || p->n_sub > 1024 || p->m < 2 || p->m > 256 || p->dom_sub < 1 || p->halo < 0 ||
         !(p->sigma > 0) || !(std::fabs(p->ar2_a) < 1.0) || !(p->ar1_a + p->ar2_a < 1.0) ||
         !(p->ar2_a - p->ar1_a < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
@@ -233,7 +251,9 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
     size_t b = 4 * (h.own_off.size() + h.own.size() + h.obs_off.size() + h.obs_sub.size() +
                     h.obs_corner.size() + h.halo_off.size() + h.halo.size() + h.order.size());
     b += 2 * n * row + na * row + 4 + 4 + 16;
-    if (p->path == LETKF_PATH_PLAIN) {
+    if (p->path == LETKF_PATH_GLOBAL) {
+        // the common part and the noise buffers only; the path's own buffers are added below
+    } else if (p->path == LETKF_PATH_PLAIN) {
         size_t acc = 0;
         for (size_t d = 0; d < nd; ++d) acc += 2 * (size_t)(h.obs_off[d + 1] - h.obs_off[d]);
         b += 4 * nd + std::max<size_t>(acc, 1) * row + std::max<size_t>(acc, 1) * eb;
@@ -255,6 +275,7 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
         b += na * na * eb + na * row;
     }
     if (p->piston != LETKF_PISTON_OFF) b += letkf::piston_bytes(h, (int)nd, (int)eb);
+    if (p->path == LETKF_PATH_GLOBAL) b += letkf::global_bytes(h.n_act, h.n_subv, p->m, p->q_sqrt != nullptr);
     return b;
 }
 
@@ -269,7 +290,7 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     c->m_pad = (eb == 8) ? ((c->m + 1) / 2) * 2 : ((c->m + 3) / 4) * 4;
     CU(cudaSetDevice(c->device));
     CU(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
-    build_model(c->host, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    build_for(c->host, p);
     HostModel& h = c->host;
     c->n_act = h.n_act; c->n_subv = h.n_subv; c->n = 2 * h.n_act; c->p = 2 * h.n_subv;
     c->n_dom = (int)h.own_off.size() - 1;
@@ -293,7 +314,9 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     if ((rc = alloc(c, (void**)&c->d_queue, 4 * sizeof(int)))) return rc;
     if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     if (cublasSetStream(c->cublas, c->stream) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
-    if (c->path == LETKF_PATH_PLAIN) {
+    if (c->path == LETKF_PATH_GLOBAL) {
+        // buffers after the initial ensemble (they need the device noise factor)
+    } else if (c->path == LETKF_PATH_PLAIN) {
         std::vector<int> so(c->n_dom);
         int acc = 0;
         for (int d = 0; d < c->n_dom; ++d) {
@@ -312,6 +335,8 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     }
     if ((rc = letkf::init_ensemble(c, p->q_sqrt, p->p0_sqrt))) return rc;
     if ((rc = letkf::piston_prepare(c))) return rc;
+    c->lq_lower = p->q_sqrt && letkf::lower_triangular(p->q_sqrt, c->n_act);
+    if (c->path == LETKF_PATH_GLOBAL && (rc = letkf::global_prepare(c))) return rc;
     CU(cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->phase = 0;
@@ -367,7 +392,7 @@ int letkf_footprint(const letkf_params* p, unsigned long long* bytes) {
     *bytes = 0;
     if (validate(p)) return LETKF_EINVAL;
     letkf::HostModel h;
-    build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    build_for(h, p);
     if (h.n_act == 0 || h.own_off.size() < 2) return LETKF_EINVAL;
     *bytes = footprint_bytes(p, h);
     return LETKF_OK;
@@ -377,7 +402,7 @@ int letkf_piston_operator(const letkf_params* p, double* K, int* n_dom) {
     if (!p || !n_dom) return LETKF_EINVAL;
     if (validate(p)) return LETKF_EINVAL;
     letkf::HostModel h;
-    build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    build_for(h, p);
     const int nd = (int)h.own_off.size() - 1;
     if (h.n_act == 0 || nd < 1) return LETKF_EINVAL;
     *n_dom = nd;
@@ -394,7 +419,7 @@ int letkf_domain_tables(const letkf_params* p, letkf_domain_sizes* sz, int* own_
     if (!p || !sz) return LETKF_EINVAL;
     if (validate(p)) return LETKF_EINVAL;
     letkf::HostModel h;
-    build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+    build_for(h, p);
     const int nd = (int)h.own_off.size() - 1;
     if (h.n_act == 0 || nd < 1) return LETKF_EINVAL;
     sz->n_sub = p->n_sub;
@@ -460,6 +485,8 @@ int letkf_analyze(letkf_ctx* c, const void* y, double sigma) {
     int rc;
     if (c->path == LETKF_PATH_PLAIN) {
         rc = letkf::plain_analyze(c, y, sigma);
+    } else if (c->path == LETKF_PATH_GLOBAL) {
+        rc = letkf::global_analyze(c, y, sigma);
     } else {
         rc = letkf::fused_step(c, y, sigma, nullptr, 0);
     }
@@ -472,7 +499,8 @@ int letkf_analyze(letkf_ctx* c, const void* y, double sigma) {
 int letkf_forecast(letkf_ctx* c, const void* v) {
     if (!c) return LETKF_EINVAL;
     CU(cudaSetDevice(c->device));
-    int rc = letkf::launch_forecast(c, v, nullptr, c->phase);
+    int rc = c->path == LETKF_PATH_GLOBAL ? letkf::global_forecast(c, v, nullptr, c->phase)
+                                          : letkf::launch_forecast(c, v, nullptr, c->phase);
     if (rc) return rc;
     c->phase = 0;
     c->frame += 1;
@@ -491,6 +519,10 @@ int letkf_step(letkf_ctx* c, const void* y, double sigma, void* xpred) {
         if ((rc = letkf::plain_analyze(c, y, sigma))) return rc;
         c->cur ^= 1;
         if ((rc = letkf::launch_forecast(c, nullptr, xp, 1))) return rc;
+    } else if (c->path == LETKF_PATH_GLOBAL) {
+        if ((rc = letkf::global_analyze(c, y, sigma))) return rc;
+        c->cur ^= 1;
+        if ((rc = letkf::global_forecast(c, nullptr, xp, 1))) return rc;
     } else {
         if ((rc = letkf::fused_step(c, y, sigma, xp, 1))) return rc;
         c->cur ^= 1;

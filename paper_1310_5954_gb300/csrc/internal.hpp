@@ -34,6 +34,8 @@ struct DomainTables {
     int* order = nullptr;       // [n_dom] processing order, most expensive first
 };
 
+struct GlobalState;   // global.cu: buffers and graph of the global path
+
 // Host copy of the geometry and domains.
 struct HostModel {
     int n_sub = 0;
@@ -116,6 +118,9 @@ struct letkf_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t cap_stream = nullptr;      // capture only
     cublasHandle_t cublas_cap = nullptr;
+    // global path (one domain, tiled tensor-core products)
+    letkf::GlobalState* gstate = nullptr;
+    int lq_lower = 0;               // the process-noise factor is lower triangular
     // differential-piston removal: per-domain entries of the boundary subapertures, the
     // least-squares operator K (n_dom x n_dom), per-domain residual sums and the raw prediction
     int piston = 0;
@@ -166,6 +171,13 @@ struct NormalsNode {
 };
 int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
 
+// global.cu: the global (single-domain) ETKF at large ensemble sizes
+size_t global_bytes(int n_act, int n_subv, int m, bool dense);
+int global_prepare(letkf_ctx* c);
+void global_free(letkf_ctx* c);
+int global_analyze(letkf_ctx* c, const void* y, double sigma);
+int global_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis);
+
 // gemm.cu: tiled tensor-core GEMM, C = A B^T with tiled BF16 operands (128 x 64 tiles)
 enum GemmEpilogue { GEMM_EPI_F32 = 0, GEMM_EPI_TILES = 1, GEMM_EPI_ADD_ROW = 2 };
 struct GemmArgs {
@@ -176,6 +188,9 @@ struct GemmArgs {
     int a_nkb, b_nkb;           // column tiles per row tile of A and B
     int nkb;                    // K / 64 steps to run
     int split;                  // 1: hi hi + hi lo + lo hi
+    int a_lower;                // 1: A is lower triangular (K steps past the row tile skipped)
+    int b_mn;                   // 1: B is the second factor M itself (tiles of M, rows = K), read
+                                //    MN-major: C = A M (BN = 64 only); 0: C = A B^T
     int M, N;                   // valid rows / columns of C
     int mode;                   // GemmEpilogue
     float* c;                   // F32 / ADD_ROW: C[row * ldc + col]

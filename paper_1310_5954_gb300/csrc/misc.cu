@@ -80,23 +80,32 @@ __global__ void forecast_kernel(T* __restrict__ X, const T* __restrict__ V, int 
         T* x1 = X + (size_t)j * m_pad;
         T* x2 = X + (size_t)(n_act + j) * m_pad;
         T s = 0;
-        for (int i = lane; i < m; i += 32) {
-            T v1 = x1[i];
-            if (!skip) {
-                T v = 0;
-                if (vmode == 0) {
-                    v = V[(size_t)j * vld + i];
-                } else if (vmode == 1) {
-                    T z[4];
-                    normals4<T>(seed, 1u, frame, (uint32_t)i, (uint32_t)(j >> 2), z);
-                    v = q_white * z[j & 3];
-                }
-                const T v2 = x2[i];
-                x2[i] = v1;
-                v1 = a * v1 + a2 * v2 + v;
-                x1[i] = v1;
+        // four members per lane per pass, their loads issued before any store (large ensembles)
+        for (int i0 = lane; i0 < m; i0 += 128) {
+            T v1[4], v2[4], v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                v1[u] = i < m ? x1[i] : (T)0;
+                v2[u] = (i < m && !skip) ? x2[i] : (T)0;
+                v[u] = (i < m && !skip && vmode == 0) ? V[(size_t)j * vld + i] : (T)0;
             }
-            s += v1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                if (i >= m) continue;
+                if (!skip) {
+                    if (vmode == 1) {
+                        T z[4];
+                        normals4<T>(seed, 1u, frame, (uint32_t)i, (uint32_t)(j >> 2), z);
+                        v[u] = q_white * z[j & 3];
+                    }
+                    x2[i] = v1[u];
+                    v1[u] = a * v1[u] + a2 * v2[u] + v[u];
+                    x1[i] = v1[u];
+                }
+                s += v1[u];
+            }
         }
         s = warp_sum(s);
         if (xpred && lane == 0) xpred[j] = s / (T)m;

@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 
 _PREC = {"fp64": _lib.LETKF_PREC_FP64, "fp32": _lib.LETKF_PREC_FP32, "mixed": _lib.LETKF_PREC_MIXED}
-_PATH = {"plain": _lib.LETKF_PATH_PLAIN, "fused": _lib.LETKF_PATH_FUSED}
+_PATH = {"plain": _lib.LETKF_PATH_PLAIN, "fused": _lib.LETKF_PATH_FUSED, "global": _lib.LETKF_PATH_GLOBAL}
 _PISTON = {"off": _lib.LETKF_PISTON_OFF, "output": _lib.LETKF_PISTON_OUTPUT, "in_loop": _lib.LETKF_PISTON_IN_LOOP}
 
 
@@ -139,6 +139,10 @@ class LETKF:
     def profile(self, enable: bool):
         """Start (True) or stop (False) stage timing; stopping returns {stage: (ms, launches)}."""
         return _lib.letkf_profile(self.ctx, 1 if enable else 0)
+
+    def global_stats(self):
+        """Global path: (Newton-Schulz steps, spectral bound s) of the last analysis."""
+        return _lib.letkf_global_stats(self.ctx)
 
     def set_graph(self, enable: bool) -> None:
         """Fused path: run each step as one CUDA graph launch, or as separate launches (default)."""

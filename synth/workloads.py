@@ -149,6 +149,14 @@ WORKLOADS = {
     "elt-80x80": _wl(2, name="elt-80x80", n_sub=80, obstruction=0.28, m=100, dom_sub=4, halo=2,
                      ar1_a=0.995, sigma=0.2, tel_diam=40.0, d_over_r0=40.0, L0=25.0, wind=15.0,
                      frame_rate=1000.0, n_frames=5000),
+    # Global ETKF (one domain), the paper's 16 m case: 32x32 unobstructed, n = 1754, 197 members.
+    "etkf-16m": _wl(5, name="etkf-16m", n_sub=32, obstruction=0.0, m=197, dom_sub=32, halo=0,
+                    ar1_a=0.99, sigma=0.1, tel_diam=16.0, d_over_r0=20.0, L0=25.0, wind=10.0,
+                    frame_rate=1000.0, n_frames=2000),
+    # Global ETKF at ELT scale with a large ensemble: the 80x80 system above, 1024 members.
+    "etkf-elt-m1024": _wl(6, name="etkf-elt-m1024", n_sub=80, obstruction=0.28, m=1024, dom_sub=80, halo=0,
+                          ar1_a=0.995, sigma=0.2, tel_diam=40.0, d_over_r0=40.0, L0=25.0, wind=15.0,
+                          frame_rate=1000.0, n_frames=5000),
     # The same ELT system under a non-stationary schedule (see Workload methods).
     "elt-80x80-nonstationary": _wl(3, name="elt-80x80-nonstationary", n_sub=80, obstruction=0.28,
                                    m=100, dom_sub=4, halo=2, ar1_a=0.995, sigma=0.1, tel_diam=40.0,

@@ -1,6 +1,6 @@
 """The tiled tensor-core GEMM (letkf_gemm_selftest) against an FP64 product: C = A B^T for FP32
-A (M x K) and B (N x K), ragged and tile-aligned shapes, both CTA tile widths, single BF16 and the
-three-product split.  Bound per element, from the arithmetic: the operands' representation error
+A (M x K) and B (N x K), ragged and tile-aligned shapes, both CTA tile widths, B read K-major or
+(given as K x N) MN-major, single BF16 and the three-product split.  Bound per element, from the arithmetic: the operands' representation error
 (2^-9 per BF16 operand; 3 x 2^-17 for the split) plus FP32 accumulation over K terms (K 2^-24),
 times sum_k |A_ik| |B_jk|."""
 
@@ -23,16 +23,17 @@ def _built():
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (200, 130, 100), (1, 1, 1), (300, 257, 1000),
                                    (1025, 1025, 9264), (2048, 1024, 1024)])
 @pytest.mark.parametrize("split", [0, 1])
-@pytest.mark.parametrize("bn", [64, 128])
-def test_gemm_matches_fp64(M, N, K, split, bn):
+@pytest.mark.parametrize("bn,b_mn", [(64, 0), (128, 0), (64, 1)])
+def test_gemm_matches_fp64(M, N, K, split, bn, b_mn):
     rng = np.random.default_rng(M * 7 + N * 3 + K)
     A = rng.standard_normal((M, K)).astype(np.float32)
     B = (rng.standard_normal((N, K)) * 2.0 + 0.5).astype(np.float32)
     a = torch.as_tensor(A, device="cuda")
-    b = torch.as_tensor(B, device="cuda")
+    # b_mn: B handed over as its transpose (K x N) and read MN-major, C = A (B^T)
+    b = torch.as_tensor(np.ascontiguousarray(B.T) if b_mn else B, device="cuda")
     c = torch.full((M, N), np.nan, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
-    rc = _lib.load().letkf_gemm_selftest(a.data_ptr(), b.data_ptr(), c.data_ptr(), M, N, K, split, bn, st)
+    rc = _lib.load().letkf_gemm_selftest(a.data_ptr(), b.data_ptr(), c.data_ptr(), M, N, K, split, bn, b_mn, st)
     assert rc == 0
     C = c.cpu().numpy().astype(np.float64)
     ref = A.astype(np.float64) @ B.astype(np.float64).T

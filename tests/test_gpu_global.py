@@ -1,0 +1,133 @@
+"""The global ETKF path (LETKF_PATH_GLOBAL; Sect. 2.2, one domain, large ensembles) against the FP64
+oracle's global ETKF, through the C ABI: one analysis from the same initial ensemble, free-running
+predictions, a rejected frame, the split analyze/forecast calls, and the device footprint.
+
+Bound, from the arithmetic: the inverse square root is iterated on A_s = (I + G/(m-1))/s, whose
+iterates hold entries from ~1 up to sqrt(kappa) (kappa = cond(I + G/(m-1))); every product rounds
+its operands to split BF16 (~2^-16 of the largest entries), so the transform carries a relative
+error ~ sqrt(kappa) 2^-16.  The tests allow 4 sqrt(kappa) 2^-16 (at least 1e-4), kappa taken from
+the oracle's ensemble at the first frame (the worst: the initial ensemble is the widest)."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import etkf
+from paper_1310_5954_gb300 import LETKF, _lib, footprint
+from paper_1310_5954_gb300 import build as builder
+
+from _gpu_common import model, rel, slopes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    builder.build()
+    _lib.load()
+
+
+def _kw(name, m=None, dense=True):
+    w, g, doms, L, Ls = model(name, m)
+    kw = dict(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, obstruction=w.obstruction, p0_sqrt=Ls,
+              precision="fp32", path="global", seed=w.seed, obs_block=w.obs_block, ar2_a=w.ar2_a)
+    if dense:
+        kw["q_sqrt"] = L
+    else:
+        kw["q_white"] = 0.05
+    return kw
+
+
+def _oracle(name, m=None, dense=True):
+    w, g, doms, L, Ls = model(name, m)
+    return etkf.OracleFilter(g, None, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L if dense else None,
+                             q_white=0.0 if dense else 0.05, L_stat=Ls, obs_block=w.obs_block, a2=w.ar2_a)
+
+
+def _kappa(o, y):
+    """cond(I + G/(m-1)) of the oracle filter's current ensemble."""
+    Y = o.C @ o.X
+    S = (Y - Y.mean(axis=1, keepdims=True)) / o.sigma
+    G = S.T @ S
+    lam = np.linalg.eigvalsh(np.eye(o.m) + G / (o.m - 1))
+    return float(lam.max() / lam.min())
+
+
+def _tol(kappa):
+    return max(1e-4, 4.0 * np.sqrt(kappa) * 2.0 ** -16)
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+CASES = [("tiny-8x8", 20), ("tiny-8x8", 300), ("etkf-16m", None), ("etkf-16m", 600), ("vlt-40x40", 1000),
+         ("etkf-elt-m1024", None)]
+
+
+@pytest.mark.parametrize("name,m", CASES)
+def test_one_analysis_matches_oracle(name, m):
+    y, _ = slopes(name, 1)
+    f = LETKF(**_kw(name, m))
+    o = _oracle(name, m)
+    x0, _ = f.get_state()
+    assert rel(x0.cpu().numpy(), o.X) < 1e-5           # the same initial ensemble
+    tol = _tol(_kappa(o, y[0]))
+    f.analyze(_t(y[0]))
+    xa, _ = f.get_state()
+    xa = xa.cpu().numpy().astype(np.float64)
+    o.analyze(y[0].astype(np.float32).astype(np.float64))
+    e_mean = rel(xa.mean(axis=1), o.X.mean(axis=1))
+    e_ens = rel(xa - xa.mean(axis=1, keepdims=True), o.X - o.X.mean(axis=1, keepdims=True))
+    print(f"{name} m={f.info.m}: analysis mean {e_mean:.3e}, anomalies {e_ens:.3e}, bound {tol:.1e}")
+    assert f.sync() == 0
+    assert e_mean < tol and e_ens < tol
+    f.close()
+
+
+@pytest.mark.parametrize("name,m,frames", [("tiny-8x8", 300, 15), ("etkf-16m", None, 8)])
+def test_free_running_predictions(name, m, frames):
+    y, _ = slopes(name, frames)
+    f = LETKF(**_kw(name, m))
+    o = _oracle(name, m)
+    tol = _tol(_kappa(o, y[0]))
+    worst = 0.0
+    for k in range(frames):
+        xp = f.step(_t(y[k])).cpu().numpy().astype(np.float64)
+        xo = o.step(y[k].astype(np.float32).astype(np.float64))
+        worst = max(worst, rel(xp, xo))
+    print(f"{name} m={f.info.m}: worst free-running prediction {worst:.3e}, bound {tol:.1e}")
+    assert f.sync() == 0
+    assert worst < tol
+    f.close()
+
+
+def test_rejected_frame_and_split_calls():
+    y, _ = slopes("tiny-8x8", 3)
+    a = LETKF(**_kw("tiny-8x8", 300))
+    b = LETKF(**_kw("tiny-8x8", 300))
+    # analyze + forecast equals step, bit for bit
+    pa = a.step(_t(y[0])).cpu().numpy()
+    b.analyze(_t(y[0]))
+    b.forecast()
+    sa, _ = a.get_state()
+    sb, _ = b.get_state()
+    assert torch.equal(sa, sb)
+    # a frame with a NaN slope leaves the ensemble unchanged and is reported
+    bad = y[1].copy()
+    bad[7] = np.nan
+    a.analyze(_t(bad))
+    s1, _ = a.get_state()
+    assert torch.equal(s1, sa)
+    assert a.sync() == _lib.LETKF_ENONFINITE
+    assert np.isfinite(pa).all()
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("name,m,dense", [("tiny-8x8", 300, True), ("tiny-8x8", 20, False), ("etkf-16m", None, True)])
+def test_footprint_equals_allocated_bytes(name, m, dense):
+    kw = _kw(name, m, dense)
+    f = LETKF(**kw)
+    assert footprint(**kw) == f.info.device_bytes
+    f.close()
