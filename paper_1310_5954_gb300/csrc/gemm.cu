@@ -60,13 +60,18 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (g.run && *g.run == 0) return;
-    if (g.run_next && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
-        // this launch decides whether the next iteration runs (see GemmArgs)
-        const float d = __uint_as_float(*g.run_dev);
-        *g.run_next = d >= g.run_tol ? 1 : 0;
-        if (g.z_final) *g.z_final = g.z_index;
+    if (g.next_flag && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        // this launch decides whether the next step runs (see GemmArgs), also when it does
+        // nothing itself, so that a finished iteration stays finished
+        const bool on = g.run == nullptr || *g.run != 0;
+        *g.next_flag = (on && __uint_as_float(*g.dev_in) >= g.run_tol) ? 1 : 0;
+        if (on) {
+            *g.dev_in = 0u;
+            if (g.z_final) *g.z_final = g.z_index;
+            if (g.steps) *g.steps += 1;
+        }
     }
+    if (g.run && *g.run == 0) return;
     const int row0 = blockIdx.y * 128, col0 = blockIdx.x * BN;
     // a lower-triangular A has no nonzero column beyond its rows
     const int nkb = g.a_lower ? min(g.nkb, 2 * ((int)blockIdx.y + 1)) : g.nkb;

@@ -14,15 +14,17 @@
 // (FP32-level, ~2^-16 per element).  The iteration's products are true products (the second
 // factor's tiles read MN-major): the matrices are symmetric in exact arithmetic, but taking
 // A B^T for A B lets the rounding's antisymmetric part grow until the iteration diverges at the
-// conditioning of the first frames (s ~ 1e4).  The iteration runs at most NS_MAX steps and stops once max |P - I| < NS_TOL (the deciding flag is
-// written on the device; the products of a finished iteration return at once); the steps are one
-// CUDA graph, launched every frame.
+// conditioning of the first frames (s ~ 1e4).  The iteration runs at most NS_MAX steps and stops
+// once max |P - I| < NS_TOL (the deciding flag is written on the device; the products of a
+// finished iteration return at once; ST_NOCONV when the limit stops it); the steps are one CUDA
+// graph, launched every frame.
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "../../include/letkf.h"
@@ -34,6 +36,8 @@ namespace letkf {
 
 constexpr int NS_MAX = 24;
 constexpr float NS_TOL = 1e-3f;
+// device control words: run[k] (step k runs) for k = 0 .. NS_MAX, steps taken, final Z buffer
+enum { CTL_RUN = 0, CTL_STEPS = NS_MAX + 1, CTL_ZFINAL = NS_MAX + 2, CTL_N = NS_MAX + 4 };
 
 struct GlobalState {
     int mr = 0, pk = 0, mp = 0, nr = 0, ka = 0;   // padded sizes: S' rows, slopes, m, state rows, actuators
@@ -46,9 +50,8 @@ struct GlobalState {
     uint8_t *l_hi = nullptr, *l_lo = nullptr;      // L tiles (rup(n_act) x ka)
     uint8_t *xi_hi = nullptr, *xi_lo = nullptr;    // xi^T tiles (mp x ka)
     float *xbar = nullptr, *rowsq = nullptr, *wbar = nullptr, *u = nullptr, *r = nullptr, *scal = nullptr;
-    int* run = nullptr;                            // [NS_MAX + 1]
-    unsigned int* dev = nullptr;                   // [NS_MAX]
-    int* zfinal = nullptr;
+    int* ctl = nullptr;                            // control words (CTL_*)
+    unsigned int* dev = nullptr;                   // [NS_MAX]: max |P - I| of each step
     int4* corner = nullptr;                        // per valid subaperture: its four corner actuators
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -154,7 +157,7 @@ __global__ void gl_rowsq_kernel(const float* __restrict__ G, int ld, int m, floa
 __global__ void gl_build_kernel(const float* __restrict__ G, int ld, int m, int mp, const float* __restrict__ rowsq,
                                 float c, uint8_t* __restrict__ as_hi, uint8_t* __restrict__ as_lo,
                                 uint8_t* __restrict__ t_hi, uint8_t* __restrict__ t_lo, float* __restrict__ scal,
-                                int* __restrict__ run, unsigned int* __restrict__ dev, int* __restrict__ zfinal,
+                                int* __restrict__ ctl, unsigned int* __restrict__ dev,
                                 const int* __restrict__ frame_bad) {
     __shared__ float s_sh;
     if (threadIdx.x < 32) {
@@ -167,10 +170,11 @@ __global__ void gl_build_kernel(const float* __restrict__ G, int ld, int m, int 
     const float s = s_sh;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         scal[0] = s;
-        for (int k = 0; k <= NS_MAX; ++k) run[k] = 0;
-        run[1] = *frame_bad ? 0 : 1;
+        for (int k = 0; k <= NS_MAX; ++k) ctl[CTL_RUN + k] = 0;
+        ctl[CTL_RUN + 1] = *frame_bad ? 0 : 1;
+        ctl[CTL_STEPS] = 1;      // the product-free first step
+        ctl[CTL_ZFINAL] = 1;     // Z_1 = T_0, in Z buffer 1
         for (int k = 0; k < NS_MAX; ++k) dev[k] = 0u;
-        *zfinal = 1;
     }
     const int g8 = mp >> 3;
     const size_t total = (size_t)mp * g8;
@@ -209,7 +213,17 @@ __global__ void gl_gemv_kernel(const uint8_t* __restrict__ z0_hi, const uint8_t*
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
         float s = 0.f;
-        for (int j = lane; j < m; j += 32) s += tval(zh, zl, toff(i, j, nkb)) * v[j];
+        // eight consecutive columns per lane and pass: one 16-byte load from each of hi and lo
+        for (int j0 = 8 * lane; j0 < m; j0 += 256) {
+            const size_t off = toff(i, j0, nkb);
+            const uint4 hv = *reinterpret_cast<const uint4*>(zh + off);
+            const uint4 lv = *reinterpret_cast<const uint4*>(zl + off);
+            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&hv);
+            const __nv_bfloat16* lb = reinterpret_cast<const __nv_bfloat16*>(&lv);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < m) s += (__bfloat162float(hb[q]) + __bfloat162float(lb[q])) * v[j0 + q];
+        }
         s = warp_sum(s);
         if (lane == 0) out[i] = (accumulate ? out[i] : 0.f) + scale * s;
     }
@@ -234,17 +248,17 @@ __global__ void gl_bcol_kernel(const float* __restrict__ G, int ld, int m, float
 }
 
 // W^T tiles: element (j, k) = w_bar[k] + Z[j][k] / sqrt(s) for j, k < m (W = w_bar 1^T + T_a; T_a
-// symmetric); latches ST_NOCONV if the iteration was still running at its step limit.
+// symmetric); latches ST_NOCONV if the step limit stopped the iteration.
 __global__ void gl_wt_kernel(const uint8_t* __restrict__ z0_hi, const uint8_t* __restrict__ z0_lo,
                              const uint8_t* __restrict__ z1_hi, const uint8_t* __restrict__ z1_lo,
                              const int* __restrict__ zfinal, int m, int mp, const float* __restrict__ wbar,
-                             const float* __restrict__ scal, const int* __restrict__ run, uint8_t* __restrict__ hi,
+                             const float* __restrict__ scal, const int* __restrict__ noconv, uint8_t* __restrict__ hi,
                              uint8_t* __restrict__ lo, int* __restrict__ status) {
     const int odd = *zfinal & 1;
     const uint8_t* zh = odd ? z1_hi : z0_hi;
     const uint8_t* zl = odd ? z1_lo : z0_lo;
     const float rs = rsqrtf(scal[0]);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && run[NS_MAX]) atomicOr(status, ST_NOCONV);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *noconv) atomicOr(status, ST_NOCONV);
     const int nkb = mp >> 6, g8 = mp >> 3;
     const size_t total = (size_t)mp * g8;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -325,61 +339,67 @@ GemmArgs gemm_args(const uint8_t* ah, const uint8_t* al, const uint8_t* bh, cons
     return g;
 }
 
-// The Newton-Schulz steps after the first (all buffers fixed per context): captured once into a
-// CUDA graph.
-int ns_launches(letkf_ctx* c, GlobalState* S, cudaStream_t s) {
-    const int m = c->m, nkb = S->mp >> 6;
-    const int bn = 64;   // true products: the second factor is read MN-major, 64 columns per CTA
-    const int mt = S->mp / 128, nt = (m + bn - 1) / bn;
+// Newton-Schulz step k from buffers a to b: P = Z_a Y_a -> T (max |P - I| into dev[k]),
+// Y_b = Y_a T, Z_b = T Z_a, all gated by run[k]; the Y product sets run[k + 1].
+int ns_step(letkf_ctx* c, GlobalState* S, int a, int k, cudaStream_t s) {
+    const int m = c->m, nkb = S->mp >> 6, b = a ^ 1;
+    const int mt = S->mp / 128, nt = (m + 63) / 64;
     int rc;
-    // Y_1 = A_s T_0 (Z_1 = T_0 was written by the builder)
+    GemmArgs g = gemm_args(S->z_hi[a], S->z_lo[a], S->y_hi[a], S->y_lo[a], nkb, m, m, c->d_status);
+    g.mode = GEMM_EPI_TILES;
+    g.o_hi = S->t_hi;
+    g.o_lo = S->t_lo;
+    g.o_nkb = nkb;
+    g.alpha = -0.5f;
+    g.beta = 1.5f;
+    g.dev = S->dev + k;
+    g.b_mn = 1;
+    g.run = S->ctl + CTL_RUN + k;
+    if ((rc = gemm_launch(g, 64, mt, nt, s))) return rc;
+    g = gemm_args(S->y_hi[a], S->y_lo[a], S->t_hi, S->t_lo, nkb, m, m, c->d_status);
+    g.mode = GEMM_EPI_TILES;
+    g.o_hi = S->y_hi[b];
+    g.o_lo = S->y_lo[b];
+    g.o_nkb = nkb;
+    g.b_mn = 1;
+    g.run = S->ctl + CTL_RUN + k;
+    g.next_flag = S->ctl + CTL_RUN + k + 1;
+    g.dev_in = S->dev + k;
+    g.run_tol = NS_TOL;
+    g.z_final = S->ctl + CTL_ZFINAL;
+    g.z_index = b;
+    g.steps = S->ctl + CTL_STEPS;
+    if ((rc = gemm_launch(g, 64, mt, nt, s))) return rc;
+    g = gemm_args(S->t_hi, S->t_lo, S->z_hi[a], S->z_lo[a], nkb, m, m, c->d_status);
+    g.mode = GEMM_EPI_TILES;
+    g.o_hi = S->z_hi[b];
+    g.o_lo = S->z_lo[b];
+    g.o_nkb = nkb;
+    g.b_mn = 1;
+    g.run = S->ctl + CTL_RUN + k;
+    return gemm_launch(g, 64, mt, nt, s);
+}
+
+// The iteration as one graph: Y_1 = A_s T_0 (Z_1 = T_0 was written by the builder), then steps
+// 1 .. NS_MAX - 1 (buffers alternate); the launches of steps after convergence return at once.
+// (Measured: conditional graph nodes around the later steps cost more than these launches.)
+int build_ns_graph(letkf_ctx* c, GlobalState* S) {
+    const int m = c->m, nkb = S->mp >> 6;
+    if (cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LETKF_ECUDA;
     GemmArgs g = gemm_args(S->as_hi, S->as_lo, S->z_hi[1], S->z_lo[1], nkb, m, m, c->d_status);
     g.mode = GEMM_EPI_TILES;
     g.o_hi = S->y_hi[1];
     g.o_lo = S->y_lo[1];
     g.o_nkb = nkb;
     g.b_mn = 1;
-    g.run = S->run + 1;
-    if ((rc = gemm_launch(g, bn, mt, nt, s))) return rc;
-    for (int k = 1; k < NS_MAX; ++k) {
-        const int a = k & 1, b = a ^ 1;
-        // P_k = Z_k Y_k -> T_k = (3I - P_k)/2, deviation max |P_k - I|
-        g = gemm_args(S->z_hi[a], S->z_lo[a], S->y_hi[a], S->y_lo[a], nkb, m, m, c->d_status);
-        g.mode = GEMM_EPI_TILES;
-        g.o_hi = S->t_hi;
-        g.o_lo = S->t_lo;
-        g.o_nkb = nkb;
-        g.alpha = -0.5f;
-        g.beta = 1.5f;
-        g.dev = S->dev + k;
-        g.b_mn = 1;
-        g.run = S->run + k;
-        if ((rc = gemm_launch(g, bn, mt, nt, s))) return rc;
-        // Y_{k+1} = Y_k T_k; this launch also decides whether step k + 1 runs
-        g = gemm_args(S->y_hi[a], S->y_lo[a], S->t_hi, S->t_lo, nkb, m, m, c->d_status);
-        g.mode = GEMM_EPI_TILES;
-        g.o_hi = S->y_hi[b];
-        g.o_lo = S->y_lo[b];
-        g.o_nkb = nkb;
-        g.b_mn = 1;
-        g.run = S->run + k;
-        g.run_next = S->run + k + 1;
-        g.run_dev = S->dev + k;
-        g.run_tol = NS_TOL;
-        g.z_final = S->zfinal;
-        g.z_index = k + 1;
-        if ((rc = gemm_launch(g, bn, mt, nt, s))) return rc;
-        // Z_{k+1} = T_k Z_k
-        g = gemm_args(S->t_hi, S->t_lo, S->z_hi[a], S->z_lo[a], nkb, m, m, c->d_status);
-        g.mode = GEMM_EPI_TILES;
-        g.o_hi = S->z_hi[b];
-        g.o_lo = S->z_lo[b];
-        g.o_nkb = nkb;
-        g.b_mn = 1;
-        g.run = S->run + k;
-        if ((rc = gemm_launch(g, bn, mt, nt, s))) return rc;
-    }
-    return LETKF_OK;
+    g.run = S->ctl + CTL_RUN + 1;
+    int rc = gemm_launch(g, 64, S->mp / 128, (m + 63) / 64, S->cap);
+    for (int k = 1; k < NS_MAX && !rc; ++k) rc = ns_step(c, S, k & 1, k, S->cap);
+    cudaGraph_t G = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(S->cap, &G);
+    if (G) S->graph = G;
+    if (rc || e != cudaSuccess || !G) return rc ? rc : LETKF_ECUDA;
+    return cudaGraphInstantiate(&S->exec, G, 0) == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
 }
 
 }  // namespace
@@ -391,7 +411,7 @@ size_t global_bytes(int n_act, int n_subv, int m, bool dense) {
     size_t b = 2 * tiled_bytes(mr, pk) + (size_t)(m + 1) * (m + 1) * 4 + 12 * tiled_bytes(mp, mp) +
                2 * tiled_bytes(nr, mp) + 2 * tiled_bytes(mp, mp);
     if (dense) b += 2 * tiled_bytes(rup(n_act, 128), ka) + 2 * tiled_bytes(mp, ka);
-    b += (size_t)2 * n_act * 4 + (size_t)4 * m * 4 + 16 + (NS_MAX + 1) * 4 + NS_MAX * 4 + 4 + (size_t)n_subv * 16;
+    b += (size_t)2 * n_act * 4 + (size_t)4 * m * 4 + 16 + CTL_N * 4 + NS_MAX * 4 + (size_t)n_subv * 16;
     return b;
 }
 
@@ -430,8 +450,8 @@ int global_prepare(letkf_ctx* c) {
     }
     ok = ok && get((size_t)c->n * 4, (void**)&S->xbar) && get((size_t)m * 4, (void**)&S->rowsq) &&
          get((size_t)m * 4, (void**)&S->wbar) && get((size_t)m * 4, (void**)&S->u) && get((size_t)m * 4, (void**)&S->r) &&
-         get(16, (void**)&S->scal) && get((NS_MAX + 1) * 4, (void**)&S->run) && get(NS_MAX * 4, (void**)&S->dev) &&
-         get(4, (void**)&S->zfinal) && get((size_t)c->n_subv * 16, (void**)&S->corner);
+         get(16, (void**)&S->scal) && get(CTL_N * 4, (void**)&S->ctl) && get(NS_MAX * 4, (void**)&S->dev) &&
+         get((size_t)c->n_subv * 16, (void**)&S->corner);
     if (!ok) return LETKF_ENOMEM;
     // corner actuators of every valid subaperture: (r,c) (r,c+1) (r+1,c) (r+1,c+1)
     const HostModel& h = c->host;
@@ -456,18 +476,9 @@ int global_prepare(letkf_ctx* c) {
                     (void*)S->y_lo[0], (void*)S->y_hi[1], (void*)S->y_lo[1], (void*)S->z_hi[0], (void*)S->z_lo[0],
                     (void*)S->z_hi[1], (void*)S->z_lo[1], (void*)S->wt_hi, (void*)S->wt_lo})
         if (cudaMemsetAsync(p, 0, tsq, c->stream) != cudaSuccess) return LETKF_ECUDA;
-    // the Newton-Schulz steps as one graph
+    // the Newton-Schulz steps as one graph with a device-side loop
     if (cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking) != cudaSuccess) return LETKF_ECUDA;
-    if (cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LETKF_ECUDA;
-    rc = ns_launches(c, S, S->cap);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(S->cap, &g);
-    if (rc || ec != cudaSuccess || !g) {
-        if (g) cudaGraphDestroy(g);
-        return rc ? rc : LETKF_ECUDA;
-    }
-    S->graph = g;
-    if (cudaGraphInstantiate(&S->exec, g, 0) != cudaSuccess) return LETKF_ECUDA;
+    if ((rc = build_ns_graph(c, S))) return rc;
     return LETKF_OK;
 }
 
@@ -512,23 +523,23 @@ int global_analyze(letkf_ctx* c, const void* yv, double sigma) {
     prof_begin(c, STAGE_EIG);
     gl_rowsq_kernel<<<grid_for((size_t)m * 32, 256), 256, 0, st>>>(S->G, m + 1, m, S->rowsq);
     gl_build_kernel<<<grid_for((size_t)S->mp * (S->mp >> 3), 256), 256, 0, st>>>(
-        S->G, m + 1, m, S->mp, S->rowsq, cm, S->as_hi, S->as_lo, S->z_hi[1], S->z_lo[1], S->scal, S->run, S->dev,
-        S->zfinal, c->d_frame_bad);
+        S->G, m + 1, m, S->mp, S->rowsq, cm, S->as_hi, S->as_lo, S->z_hi[1], S->z_lo[1], S->scal, S->ctl, S->dev,
+        c->d_frame_bad);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
     if (cudaGraphLaunch(S->exec, st) != cudaSuccess) return LETKF_ECUDA;
     // mean weights, refined once: w = Z^2 b/(cs); w += Z^2 (b - (cI + G) w)/(cs)
     const int nkb = S->mp >> 6, gv = grid_for((size_t)m * 32, 256);
     gl_bcol_kernel<<<grid_for(m, 256), 256, 0, st>>>(S->G, m + 1, m, S->r);
     for (int pass = 0; pass < 2; ++pass) {
-        gl_gemv_kernel<<<gv, 256, 0, st>>>(S->z_hi[0], S->z_lo[0], S->z_hi[1], S->z_lo[1], S->zfinal, nkb, m, S->r,
+        gl_gemv_kernel<<<gv, 256, 0, st>>>(S->z_hi[0], S->z_lo[0], S->z_hi[1], S->z_lo[1], S->ctl + CTL_ZFINAL, nkb, m, S->r,
                                            S->scal, cm, 0, 0, S->u);
-        gl_gemv_kernel<<<gv, 256, 0, st>>>(S->z_hi[0], S->z_lo[0], S->z_hi[1], S->z_lo[1], S->zfinal, nkb, m, S->u,
+        gl_gemv_kernel<<<gv, 256, 0, st>>>(S->z_hi[0], S->z_lo[0], S->z_hi[1], S->z_lo[1], S->ctl + CTL_ZFINAL, nkb, m, S->u,
                                            S->scal, cm, 1, pass, S->wbar);
         if (pass == 0) gl_resid_kernel<<<gv, 256, 0, st>>>(S->G, m + 1, m, S->wbar, cm, S->r);
     }
     gl_wt_kernel<<<grid_for((size_t)S->mp * (S->mp >> 3), 256), 256, 0, st>>>(
-        S->z_hi[0], S->z_lo[0], S->z_hi[1], S->z_lo[1], S->zfinal, m, S->mp, S->wbar, S->scal, S->run, S->wt_hi,
-        S->wt_lo, c->d_status);
+        S->z_hi[0], S->z_lo[0], S->z_hi[1], S->z_lo[1], S->ctl + CTL_ZFINAL, m, S->mp, S->wbar, S->scal,
+        S->ctl + CTL_RUN + NS_MAX, S->wt_hi, S->wt_lo, c->d_status);
     prof_end(c);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
     // transform X_a = x_bar + X' W
@@ -577,7 +588,7 @@ extern "C" int letkf_global_stats(letkf_ctx* c, int* ns_steps, double* s_bound) 
     int zf = 0;
     float sv = 0.f;
     if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess ||
-        cudaMemcpy(&zf, S->zfinal, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&zf, S->ctl + CTL_STEPS, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&sv, S->scal, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
         return LETKF_ECUDA;
     *ns_steps = zf;

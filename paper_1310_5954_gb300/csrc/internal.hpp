@@ -203,11 +203,12 @@ struct GemmArgs {
     unsigned int* dev;          // TILES: max |C - I| over valid entries (float bits, atomicMax)
     const float* add;           // ADD_ROW: per-row term
     const int* run;             // non-null: the launch does nothing when *run == 0
-    int* run_next;              // non-null: CTA (0,0) sets *run_next = (*run_dev >= run_tol)
-    const unsigned int* run_dev;
-    float run_tol;
-    int* z_final;               // non-null: CTA (0,0) sets *z_final = z_index
+    int* next_flag;             // non-null: CTA (0,0) sets *next_flag = run && (*dev_in >= run_tol),
+    unsigned int* dev_in;       //   and, when running, resets *dev_in, sets *z_final = z_index
+    float run_tol;              //   and counts one step in *steps
+    int* z_final;
     int z_index;
+    int* steps;
     int* status;
 };
 size_t tiled_bytes(int rows, int cols);
