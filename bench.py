@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-piston", action="store_true", help="skip the differential-piston leg")
     ap.add_argument("--no-global", action="store_true", help="skip the global-ETKF (m = 1024) leg")
     ap.add_argument("--global-steps", type=int, default=200, help="timed steps of the global-ETKF leg")
+    ap.add_argument("--oracle-probe", type=float, default=0.0,
+                    help="(internal) time the oracle alone for this many seconds and print frames/s")
+    ap.add_argument("--global-only", action="store_true",
+                    help="run only the global-ETKF leg and print its JSON object (profiling)")
     ap.add_argument("--piston-frames", type=int, default=600, help="frames of the differential-piston leg")
     return ap.parse_args()
 
@@ -285,7 +289,7 @@ def piston_leg(w, path, precision, L, Ls, y, phi, n_frames, flush, tuning, torch
     without correction, with the output corrected, and with the correction in the loop; per mode the
     per-step time (CUDA events, L2 flushed before each step), the residual RMS after a burn-in of
     half the frames, and the two correction kernels' share of the step."""
-    n = min(n_frames, len(y))
+    n = min(n_frames, len(y) - 1)      # the truth of frame k + 1 scores frame k's prediction
     burn = n // 2
     out = {"frames": n, "burn_in": burn, "modes": {}}
     preds_in_loop = None
@@ -528,9 +532,37 @@ def cpu_baseline_nonstationary(inp, seconds):
             "gpu": rms(inp["pred"][:nf].astype(np.float64)), "seconds": time.perf_counter() - t1}
 
 
+def oracle_probe(wname, seconds):
+    """The oracle alone on the first frames of the workload for a bounded time (run in a child
+    process whose BLAS thread count the parent sets)."""
+    from oracle import geometry
+    from synth import workload
+    w = workload(wname)
+    g = geometry.make_geometry(w.n_sub, w.obstruction)
+    L = w.process_noise_sqrt(g.act_rc)
+    Ls = w.stationary_sqrt(g.act_rc)
+    _, y, _ = workload_inputs(wname, 64, g.sub_valid, g.act_valid)
+    fps, _, nfr, dt = cpu_baseline(wname, y, seconds, L, Ls)
+    print(json.dumps({"frames_per_s": fps, "frames": nfr, "seconds": dt}))
+
+
+def oracle_single_thread(wname, seconds):
+    """cpu_baseline at one thread: the same oracle in a child process with every BLAS / OpenMP
+    thread pool limited to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", wname, "--oracle-probe", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"unavailable": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "probe failed"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.oracle_probe > 0:
+        return oracle_probe(args.workload, args.oracle_probe)
     if args.impl == "reference":
         return reference_main(args, world, rank)
     import torch
@@ -541,6 +573,10 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     from paper_1310_5954_gb300 import LETKF  # noqa: F401
+    if args.global_only:
+        flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(global_leg(args.global_steps, 5, flush, torch)))
+        return
     from synth import workload
     precision = args.precision or ("mixed" if args.path == "fused" else "fp32")
     w = workload(args.workload)
@@ -646,7 +682,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fps, opreds, nfr, dt = cpu_baseline(args.workload, y, args.cpu_seconds, L, Ls)
         out["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": f"first {nfr} frames of {w.name}, FP64 numpy/LAPACK oracle, {dt:.1f} s"}
+                               "sample": f"first {nfr} frames of {w.name}, FP64 numpy/LAPACK oracle, {dt:.1f} s",
+                               "single_thread": oracle_single_thread(args.workload, args.cpu_seconds / 2)}
         nb = min(burn, max(nfr - 2, 0))
         out["residual_rms"]["oracle_first_frames"] = {"frames": nfr, "burn_in": nb,
                                                       "oracle": residual_rms(opreds, phi, nb),

@@ -191,7 +191,7 @@ int letkf_piston_operator(const letkf_params* params, double* K, int* n_dom);
 /*
  * letkf_gemm_selftest (tests): C (M x N, row-major) = A (M x K) B (N x K)^T with A, B FP32 row-major
  * device arrays, through the library's tiled tensor-core GEMM (BF16 operands; split = 1 adds the
- * two low-part products, ~2^-16 relative per element; bn = 64 or 128 columns per CTA tile).  With
+ * two low-part products, ~2^-16 relative per element; bn = 64, 128 or 256 columns per CTA tile).  With
  * b_mn = 1 (bn = 64 only) B is given as K x N row-major and C = A B, the tiles of B read MN-major.
  * Ordered on `stream` and synchronised.  LETKF_ETIMEOUT if a bounded wait inside gave up.
  */

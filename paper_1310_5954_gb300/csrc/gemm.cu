@@ -6,7 +6,7 @@
 // to multiples of 128 and 64.  A split operand has a second, "lo", set of tiles holding
 // bf16(x - float(hi)): hi * hi + hi * lo + lo * hi reproduces an FP32 product to ~2^-16.
 //
-// C (M x N) = A (M x K) B (N x K)^T: one CTA per 128 x BN tile of C (BN = 64 or 128), K in steps
+// C (M x N) = A (M x K) B (N x K)^T: one CTA per 128 x BN tile of C (BN = 64, 128 or 256), K in steps
 // of 64 through a ring of shared-memory stages filled by 1-D bulk copies (one producer thread)
 // and consumed by tcgen05.mma issued from one thread, accumulator in tensor memory; then all four
 // warps read the accumulator back (one row per thread) for the epilogue.  A 64-row block of a B
@@ -72,9 +72,23 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
         }
     }
     if (g.run && *g.run == 0) return;
-    const int row0 = blockIdx.y * 128, col0 = blockIdx.x * BN;
-    // a lower-triangular A has no nonzero column beyond its rows
-    const int nkb = g.a_lower ? min(g.nkb, 2 * ((int)blockIdx.y + 1)) : g.nkb;
+    // the output tile: from the grid, or from a tile list (one entry per blockIdx.x)
+    int ty = blockIdx.y, tx = blockIdx.x;
+    if (g.tiles) {
+        const int2 t = g.tiles[blockIdx.x];
+        ty = t.x;
+        tx = t.y;
+    }
+    const int row0 = ty * 128, col0 = tx * BN;
+    // a lower-triangular A has no nonzero column beyond its rows; split K: blockIdx.z's share
+    const int nkb_all = g.a_lower ? min(g.nkb, 2 * (ty + 1)) : g.nkb;
+    int kb0 = 0, kb1 = nkb_all;
+    if (g.ksplit > 1) {
+        const int per = (nkb_all + g.ksplit - 1) / g.ksplit;
+        kb0 = min(nkb_all, (int)blockIdx.z * per);
+        kb1 = min(nkb_all, kb0 + per);
+    }
+    const int nkb = kb1 - kb0;
     const bool split = g.split != 0;
     const uint32_t stage_bytes = split ? L::STAGE_SPLIT : L::STAGE_SPLIT / 2;
     if (tid == 0) {
@@ -95,13 +109,16 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     // operand bases of this tile
-    const uint8_t* a_hi = g.a_hi + (size_t)blockIdx.y * g.a_nkb * TILE_B;
-    const uint8_t* a_lo = g.a_lo ? g.a_lo + (size_t)blockIdx.y * g.a_nkb * TILE_B : nullptr;
+    const uint8_t* a_hi = g.a_hi + ((size_t)ty * g.a_nkb + kb0) * TILE_B;
+    const uint8_t* a_lo = g.a_lo ? g.a_lo + ((size_t)ty * g.a_nkb + kb0) * TILE_B : nullptr;
     // B K-major (rows = N): the 128-row tile holding this CTA's columns, and its half for BN = 64.
     // B MN-major (the second factor M itself, rows = K; BN = 64): the step-kb chunk is rows
     // 64 kb .. 64 kb + 63 of column tile col0 / 64, the first or second half of that tile.
+    // BN = 256 (K-major only): two consecutive 128-row tiles, copied next to each other so that
+    // one descriptor with the same row-group stride spans all 256 rows.
     const size_t b_row_tile = g.b_mn ? (size_t)(col0 >> 6) * TILE_B : (size_t)(col0 >> 7) * g.b_nkb * TILE_B;
     const size_t b_half = (!g.b_mn && BN == 64 && (col0 & 64)) ? (size_t)L::B_BYTES : 0;
+    const size_t b_next = (size_t)g.b_nkb * TILE_B;   // the second 128-row tile of a 256-row block
     const uint8_t* b_hi = g.b_hi + b_row_tile + b_half;
     const uint8_t* b_lo = g.b_lo ? g.b_lo + b_row_tile + b_half : nullptr;
     int issued = 0;   // stages the producer filled (for the drain on abort)
@@ -115,14 +132,25 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
             }
             if (*reinterpret_cast<volatile int*>(&abort_flag)) break;
             uint8_t* st = smem + (size_t)s * L::STAGE_SPLIT;
-            const size_t boff = g.b_mn ? ((size_t)(kb >> 1) * g.b_nkb) * TILE_B + (size_t)(kb & 1) * L::B_BYTES
-                                       : (size_t)kb * TILE_B;
+            const int kg = kb0 + kb;   // the K step in the whole operand
+            const size_t boff = g.b_mn ? ((size_t)(kg >> 1) * g.b_nkb) * TILE_B + (size_t)(kg & 1) * L::B_BYTES
+                                       : (size_t)kg * TILE_B;
             mbar_arrive_expect_tx(&full[s], stage_bytes);
             bulk_g2s(st, a_hi + (size_t)kb * TILE_B, TILE_B, &full[s]);
-            bulk_g2s(st + 2 * TILE_B, b_hi + boff, L::B_BYTES, &full[s]);
+            if (BN == 256) {
+                bulk_g2s(st + 2 * TILE_B, b_hi + boff, TILE_B, &full[s]);
+                bulk_g2s(st + 3 * TILE_B, b_hi + b_next + boff, TILE_B, &full[s]);
+            } else {
+                bulk_g2s(st + 2 * TILE_B, b_hi + boff, L::B_BYTES, &full[s]);
+            }
             if (split) {
                 bulk_g2s(st + TILE_B, a_lo + (size_t)kb * TILE_B, TILE_B, &full[s]);
-                bulk_g2s(st + 2 * TILE_B + L::B_BYTES, b_lo + boff, L::B_BYTES, &full[s]);
+                if (BN == 256) {
+                    bulk_g2s(st + 2 * TILE_B + L::B_BYTES, b_lo + boff, TILE_B, &full[s]);
+                    bulk_g2s(st + 3 * TILE_B + L::B_BYTES, b_lo + b_next + boff, TILE_B, &full[s]);
+                } else {
+                    bulk_g2s(st + 2 * TILE_B + L::B_BYTES, b_lo + boff, L::B_BYTES, &full[s]);
+                }
             }
             issued = kb + 1;
         }
@@ -176,11 +204,12 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
             float v[64];
             tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
             if (g.mode == GEMM_EPI_F32) {
+                float* cz = g.c + (size_t)blockIdx.z * g.c_split_stride;
                 if (row < g.M)
 #pragma unroll
                     for (int j = 0; j < 64; ++j) {
                         const int col = col0 + c0 + j;
-                        if (col < g.N) g.c[(size_t)row * g.ldc + col] = g.alpha * v[j];
+                        if (col < g.N) cz[(size_t)row * g.ldc + col] = g.alpha * v[j];
                     }
             } else if (g.mode == GEMM_EPI_TILES) {
                 // out = alpha * acc + beta * I, as a tiled operand (all padded positions written:
@@ -254,17 +283,24 @@ int gemm_prepare() {
     if (cudaFuncSetAttribute(gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              GemmSmem<64>::BYTES) != cudaSuccess ||
         cudaFuncSetAttribute(gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             GemmSmem<128>::BYTES) != cudaSuccess)
+                             GemmSmem<128>::BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GemmSmem<256>::BYTES) != cudaSuccess)
         return LETKF_ECUDA;
     return LETKF_OK;
 }
 
 int gemm_launch(const GemmArgs& g, int bn, int m_tiles, int n_tiles, cudaStream_t stream) {
     if (g.b_mn && bn != 64) return LETKF_EINVAL;
+    // a split K must leave every split at least one step
+    if (g.ksplit > 1 && ((g.nkb + g.ksplit - 1) / g.ksplit) * (g.ksplit - 1) >= g.nkb) return LETKF_EINVAL;
+    const dim3 grid(n_tiles, m_tiles, g.ksplit > 1 ? g.ksplit : 1);
     if (bn == 64) {
-        gemm_kernel<64><<<dim3(n_tiles, m_tiles), GT, GemmSmem<64>::BYTES, stream>>>(g);
+        gemm_kernel<64><<<grid, GT, GemmSmem<64>::BYTES, stream>>>(g);
     } else if (bn == 128) {
-        gemm_kernel<128><<<dim3(n_tiles, m_tiles), GT, GemmSmem<128>::BYTES, stream>>>(g);
+        gemm_kernel<128><<<grid, GT, GemmSmem<128>::BYTES, stream>>>(g);
+    } else if (bn == 256) {
+        gemm_kernel<256><<<grid, GT, GemmSmem<256>::BYTES, stream>>>(g);
     } else {
         return LETKF_EINVAL;
     }
@@ -288,11 +324,12 @@ extern "C" int letkf_gemm_selftest(const float* A, const float* B, float* C, int
                                    int b_mn, void* stream) {
     using namespace letkf;
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || M > 16384 || N > 16384 || K > 65536 ||
-        (split != 0 && split != 1) || (bn != 64 && bn != 128) || (b_mn != 0 && b_mn != 1) || (b_mn && bn != 64))
+        (split != 0 && split != 1) || (bn != 64 && bn != 128 && bn != 256) || (b_mn != 0 && b_mn != 1) ||
+        (b_mn && bn != 64))
         return LETKF_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mp = (M + 127) / 128 * 128, kp = (K + 63) / 64 * 64;
-    const int np = (N + 127) / 128 * 128;
+    const int np = (N + bn - 1) / bn * bn > (N + 127) / 128 * 128 ? (N + bn - 1) / bn * bn : (N + 127) / 128 * 128;
     uint8_t *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
     int* st = nullptr;
     int rc = gemm_prepare();

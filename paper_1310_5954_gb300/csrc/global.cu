@@ -43,6 +43,9 @@ struct GlobalState {
     int mr = 0, pk = 0, mp = 0, nr = 0, ka = 0;   // padded sizes: S' rows, slopes, m, state rows, actuators
     uint8_t *st_hi = nullptr, *st_lo = nullptr;   // [S d]^T tiles (mr x pk)
     float* G = nullptr;                            // (m+1) x (m+1) Gram, row-major
+    float* Gpart = nullptr;                        // gram_split partial Grams of the upper tiles
+    int2* gram_tiles = nullptr;                    // the upper 128 x 128 tiles of the Gram
+    int gram_ntiles = 0, gram_split = 1;
     uint8_t *as_hi = nullptr, *as_lo = nullptr, *t_hi = nullptr, *t_lo = nullptr;
     uint8_t *y_hi[2] = {}, *y_lo[2] = {}, *z_hi[2] = {}, *z_lo[2] = {};
     uint8_t *xp_hi = nullptr, *xp_lo = nullptr;    // X' tiles (nr x mp)
@@ -64,6 +67,19 @@ namespace {
 constexpr int TILE_B = 128 * 64 * 2;
 
 int rup(int v, int a) { return (v + a - 1) / a * a; }
+
+// Split of the Gram's K steps: enough shares that the upper tiles fill about one wave of SMs,
+// each share at least two steps and none empty.
+int gram_split_for(int m, int p, int sms) {
+    const int rt = rup(m + 1, 128) / 128, ct = (m + 1 + 127) / 128;
+    int tiles = 0;
+    for (int r = 0; r < rt; ++r)
+        for (int c = r; c < ct; ++c) ++tiles;
+    const int nkb = rup(p, 64) / 64;
+    int ks = std::max(1, std::min(nkb / 2, sms / std::max(tiles, 1)));
+    while (ks > 1 && ((nkb + ks - 1) / ks) * (ks - 1) >= nkb) --ks;
+    return ks;
+}
 
 __device__ __forceinline__ size_t toff(int row, int col, int nkb) {
     return ((size_t)(row >> 7) * nkb + (col >> 6)) * TILE_B + umma::op_offset(row & 127, col & 63, 64);
@@ -319,6 +335,20 @@ __global__ void gl_normals_kernel(unsigned long long seed, uint32_t frame, int n
     }
 }
 
+// The Gram from its split-K partials: the upper 128 x 128 tiles were computed, the lower ones
+// are their mirror; the shares are added in order.
+__global__ void gl_gram_reduce_kernel(const float* __restrict__ part, int splits, size_t stride, int m1,
+                                      float* __restrict__ G) {
+    const size_t total = (size_t)m1 * m1;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / m1), j = (int)(t - (size_t)i * m1);
+        const size_t src = (j >> 7) >= (i >> 7) ? t : (size_t)j * m1 + i;
+        float v = 0.f;
+        for (int z = 0; z < splits; ++z) v += part[z * stride + src];
+        G[t] = v;
+    }
+}
+
 int grid_for(size_t work, int block) {
     return (int)std::max<size_t>(1, std::min<size_t>((work + block - 1) / block, 152 * 16));
 }
@@ -404,13 +434,20 @@ int build_ns_graph(letkf_ctx* c, GlobalState* S) {
 
 }  // namespace
 
-size_t global_bytes(int n_act, int n_subv, int m, bool dense) {
+size_t global_bytes(int n_act, int n_subv, int m, bool dense, int sms) {
     const int mr = rup(m + 1, 128), pk = rup(2 * n_subv, 64), mp = rup(m, 128), nr = rup(2 * n_act, 128);
     const int ka = rup(n_act, 64);
     // [S d]^T, the Gram, A_s, T, Y (2), Z (2), X', W^T (hi and lo tiles each)
     size_t b = 2 * tiled_bytes(mr, pk) + (size_t)(m + 1) * (m + 1) * 4 + 12 * tiled_bytes(mp, mp) +
                2 * tiled_bytes(nr, mp) + 2 * tiled_bytes(mp, mp);
     if (dense) b += 2 * tiled_bytes(rup(n_act, 128), ka) + 2 * tiled_bytes(mp, ka);
+    {   // split-K partials of the Gram and its tile list
+        const int rt = rup(m + 1, 128) / 128, ct = (m + 1 + 127) / 128;
+        int tiles = 0;
+        for (int r = 0; r < rt; ++r)
+            for (int c = r; c < ct; ++c) ++tiles;
+        b += (size_t)gram_split_for(m, 2 * n_subv, sms) * (m + 1) * (m + 1) * 4 + (size_t)tiles * sizeof(int2);
+    }
     b += (size_t)2 * n_act * 4 + (size_t)4 * m * 4 + 16 + CTL_N * 4 + NS_MAX * 4 + (size_t)n_subv * 16;
     return b;
 }
@@ -435,6 +472,15 @@ int global_prepare(letkf_ctx* c) {
     const size_t tst = tiled_bytes(S->mr, S->pk), tsq = tiled_bytes(S->mp, S->mp);
     ok = ok && get(tst, (void**)&S->st_hi) && get(tst, (void**)&S->st_lo);
     ok = ok && get((size_t)(m + 1) * (m + 1) * 4, (void**)&S->G);
+    std::vector<int2> gt;
+    for (int r = 0; r < S->mr / 128; ++r)
+        for (int cc = r; cc < (m + 1 + 127) / 128; ++cc) gt.push_back(make_int2(r, cc));
+    S->gram_ntiles = (int)gt.size();
+    S->gram_split = gram_split_for(m, c->p, c->sms);
+    ok = ok && get((size_t)S->gram_split * (m + 1) * (m + 1) * 4, (void**)&S->Gpart) &&
+         get(gt.size() * sizeof(int2), (void**)&S->gram_tiles);
+    if (ok && cudaMemcpy(S->gram_tiles, gt.data(), gt.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return LETKF_ECUDA;
     ok = ok && get(tsq, (void**)&S->as_hi) && get(tsq, (void**)&S->as_lo) && get(tsq, (void**)&S->t_hi) &&
          get(tsq, (void**)&S->t_lo);
     for (int q = 0; q < 2; ++q)
@@ -513,11 +559,17 @@ int global_analyze(letkf_ctx* c, const void* yv, double sigma) {
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
     // Gram [S d]^T [S d]
     prof_begin(c, STAGE_GRAM);
+    // the upper tiles only (the Gram is symmetric), K split so that they fill the SMs
     GemmArgs g = gemm_args(S->st_hi, S->st_lo, S->st_hi, S->st_lo, S->pk >> 6, m + 1, m + 1, c->d_status);
     g.mode = GEMM_EPI_F32;
-    g.c = S->G;
+    g.c = S->Gpart;
     g.ldc = m + 1;
-    if ((rc = gemm_launch(g, 128, S->mr / 128, (m + 1 + 127) / 128, st))) return rc;
+    g.tiles = S->gram_tiles;
+    g.ksplit = S->gram_split;
+    g.c_split_stride = (size_t)(m + 1) * (m + 1);
+    if ((rc = gemm_launch(g, 128, 1, S->gram_ntiles, st))) return rc;
+    gl_gram_reduce_kernel<<<grid_for((size_t)(m + 1) * (m + 1), 256), 256, 0, st>>>(
+        S->Gpart, S->gram_split, (size_t)(m + 1) * (m + 1), m + 1, S->G);
     prof_end(c);
     // inverse square root
     prof_begin(c, STAGE_EIG);
@@ -551,7 +603,9 @@ int global_analyze(letkf_ctx* c, const void* yv, double sigma) {
     g.c = Xo;
     g.ldc = c->m_pad;
     g.add = S->xbar;
-    if ((rc = gemm_launch(g, 128, S->nr / 128, (m + 127) / 128, st))) return rc;
+    // 256-column tiles where the W^T tiles have the rows (m rounded to 256): half the re-reads of X'
+    const int bt = S->mp % 256 == 0 ? 256 : 128;
+    if ((rc = gemm_launch(g, bt, S->nr / 128, (m + bt - 1) / bt, st))) return rc;
     gl_reject_kernel<<<grid_for((size_t)n * c->m_pad, 256), 256, 0, st>>>(X, Xo, (size_t)n * c->m_pad, c->d_frame_bad);
     prof_end(c);
     return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
@@ -570,7 +624,8 @@ int global_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analys
     g.mode = GEMM_EPI_F32;
     g.c = static_cast<float*>(c->V);
     g.ldc = c->m;
-    const int rc = gemm_launch(g, 128, rup(c->n_act, 128) / 128, (c->m + 127) / 128, c->stream);
+    const int bt = S->mp % 256 == 0 ? 256 : 128;
+    const int rc = gemm_launch(g, bt, rup(c->n_act, 128) / 128, (c->m + bt - 1) / bt, c->stream);
     prof_end(c);
     if (rc) return rc;
     return launch_forecast(c, c->V, xpred, in_analysis);

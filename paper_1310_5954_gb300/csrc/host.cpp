@@ -275,7 +275,11 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
         b += na * na * eb + na * row;
     }
     if (p->piston != LETKF_PISTON_OFF) b += letkf::piston_bytes(h, (int)nd, (int)eb);
-    if (p->path == LETKF_PATH_GLOBAL) b += letkf::global_bytes(h.n_act, h.n_subv, p->m, p->q_sqrt != nullptr);
+    if (p->path == LETKF_PATH_GLOBAL) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) sms = 0;
+        b += letkf::global_bytes(h.n_act, h.n_subv, p->m, p->q_sqrt != nullptr, sms);
+    }
     return b;
 }
 

@@ -172,7 +172,7 @@ struct NormalsNode {
 int normals_node_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
 
 // global.cu: the global (single-domain) ETKF at large ensemble sizes
-size_t global_bytes(int n_act, int n_subv, int m, bool dense);
+size_t global_bytes(int n_act, int n_subv, int m, bool dense, int sms);
 int global_prepare(letkf_ctx* c);
 void global_free(letkf_ctx* c);
 int global_analyze(letkf_ctx* c, const void* y, double sigma);
@@ -189,6 +189,9 @@ struct GemmArgs {
     int nkb;                    // K / 64 steps to run
     int split;                  // 1: hi hi + hi lo + lo hi
     int a_lower;                // 1: A is lower triangular (K steps past the row tile skipped)
+    const int2* tiles;          // non-null: blockIdx.x takes output tile (row tile, column tile) tiles[x]
+    int ksplit;                 // > 1: blockIdx.z takes one of ksplit contiguous shares of the K steps,
+    size_t c_split_stride;      //   F32 output of share z at c + z * c_split_stride
     int b_mn;                   // 1: B is the second factor M itself (tiles of M, rows = K), read
                                 //    MN-major: C = A M (BN = 64 only); 0: C = A B^T
     int M, N;                   // valid rows / columns of C
