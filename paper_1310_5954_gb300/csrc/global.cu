@@ -17,7 +17,7 @@
 // conditioning of the first frames (s ~ 1e4).  The iteration runs at most NS_MAX steps and stops
 // once max |P - I| < NS_TOL (the deciding flag is written on the device; the products of a
 // finished iteration return at once; ST_NOCONV when the limit stops it); the steps are one CUDA
-// graph, launched every frame.
+// graph, launched every frame, whose steps past NS_FLAT sit behind a conditional node.
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -35,6 +35,7 @@
 namespace letkf {
 
 constexpr int NS_MAX = 24;
+constexpr int NS_FLAT = 12;     // steps launched unconditionally; the rest behind one conditional node
 constexpr float NS_TOL = 1e-3f;
 // device control words: run[k] (step k runs) for k = 0 .. NS_MAX, steps taken, final Z buffer
 enum { CTL_RUN = 0, CTL_STEPS = NS_MAX + 1, CTL_ZFINAL = NS_MAX + 2, CTL_N = NS_MAX + 4 };
@@ -410,12 +411,24 @@ int ns_step(letkf_ctx* c, GlobalState* S, int a, int k, cudaStream_t s) {
     return gemm_launch(g, 64, mt, nt, s);
 }
 
-// The iteration as one graph: Y_1 = A_s T_0 (Z_1 = T_0 was written by the builder), then steps
-// 1 .. NS_MAX - 1 (buffers alternate); the launches of steps after convergence return at once.
-// (Measured: conditional graph nodes around the later steps cost more than these launches.)
+// Sets the condition of the conditional node holding the later steps: whether step k runs.
+__global__ void gl_cond_kernel(const int* __restrict__ ctl, int k, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, ctl[CTL_RUN + k] ? 1u : 0u);
+}
+
+// The iteration as one graph: Y_1 = A_s T_0 (Z_1 = T_0 was written by the builder), steps
+// 1 .. NS_FLAT - 1 in sequence (launches after convergence return at once), then the steps up to
+// NS_MAX - 1 inside one conditional node that runs only when step NS_FLAT is still needed (the
+// first frames' conditioning).  A conditional node whose condition is not set stays off.
 int build_ns_graph(letkf_ctx* c, GlobalState* S) {
     const int m = c->m, nkb = S->mp >> 6;
-    if (cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LETKF_ECUDA;
+    cudaGraph_t G = nullptr;
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return LETKF_ECUDA;
+    S->graph = G;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, G, 0u, cudaGraphCondAssignDefault) != cudaSuccess) return LETKF_ECUDA;
+    if (cudaStreamBeginCaptureToGraph(S->cap, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return LETKF_ECUDA;
     GemmArgs g = gemm_args(S->as_hi, S->as_lo, S->z_hi[1], S->z_lo[1], nkb, m, m, c->d_status);
     g.mode = GEMM_EPI_TILES;
     g.o_hi = S->y_hi[1];
@@ -424,11 +437,42 @@ int build_ns_graph(letkf_ctx* c, GlobalState* S) {
     g.b_mn = 1;
     g.run = S->ctl + CTL_RUN + 1;
     int rc = gemm_launch(g, 64, S->mp / 128, (m + 63) / 64, S->cap);
-    for (int k = 1; k < NS_MAX && !rc; ++k) rc = ns_step(c, S, k & 1, k, S->cap);
-    cudaGraph_t G = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(S->cap, &G);
-    if (G) S->graph = G;
-    if (rc || e != cudaSuccess || !G) return rc ? rc : LETKF_ECUDA;
+    for (int k = 1; k < NS_FLAT && !rc; ++k) rc = ns_step(c, S, k & 1, k, S->cap);
+    if (!rc) {
+        gl_cond_kernel<<<1, 1, 0, S->cap>>>(S->ctl, NS_FLAT, h);
+        if (cudaGetLastError() != cudaSuccess) rc = LETKF_ECUDA;
+    }
+    cudaGraph_t cap_out = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(S->cap, &cap_out);
+    if (rc || e1 != cudaSuccess) return rc ? rc : LETKF_ECUDA;
+    // the node after the last one captured
+    size_t nn = 0;
+    if (cudaGraphGetNodes(G, nullptr, &nn) != cudaSuccess || nn == 0) return LETKF_ECUDA;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(G, nodes.data(), &nn) != cudaSuccess) return LETKF_ECUDA;
+    cudaGraphNode_t last = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+        size_t out = 0;
+        if (cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &out) != cudaSuccess) return LETKF_ECUDA;
+        if (out == 0) last = nd;
+    }
+    if (!last) return LETKF_ECUDA;
+    // the parameter struct holds a union of non-trivial members: built in zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char cp_store[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_store, 0, sizeof(cp_store));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_store);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, G, &last, nullptr, 1, &cp) != cudaSuccess) return LETKF_ECUDA;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(S->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return LETKF_ECUDA;
+    for (int k = NS_FLAT; k < NS_MAX && !rc; ++k) rc = ns_step(c, S, k & 1, k, S->cap);
+    const cudaError_t e2 = cudaStreamEndCapture(S->cap, &cap_out);
+    if (rc || e2 != cudaSuccess) return rc ? rc : LETKF_ECUDA;
     return cudaGraphInstantiate(&S->exec, G, 0) == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
 }
 
