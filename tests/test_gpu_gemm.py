@@ -21,7 +21,7 @@ def _built():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (200, 130, 100), (1, 1, 1), (300, 257, 1000),
-                                   (1025, 1025, 9264), (2048, 1024, 1024)])
+                                   (1025, 1025, 9264), (2048, 1024, 1024), (1024, 1024, 1024)])
 @pytest.mark.parametrize("split", [0, 1])
 @pytest.mark.parametrize("bn,b_mn", [(64, 0), (128, 0), (256, 0), (64, 1)])
 def test_gemm_matches_fp64(M, N, K, split, bn, b_mn):
