@@ -206,6 +206,15 @@ int letkf_gemm_selftest(const float* A, const float* B, float* C, int M, int N, 
  */
 int letkf_global_stats(letkf_ctx* ctx, int* ns_steps, double* s_bound);
 
+/*
+ * letkf_set_domain_mask (fault injection, local paths): active[d] == 0 skips domain d from the
+ * next analysis on: its actuators keep their forecast, as a domain without observations does
+ * (Sect. 2.3; a lost node of a distributed implementation).  active has n_dom entries in the
+ * numbering of letkf_domain_tables; NULL restores every domain.  Synchronises the stream;
+ * LETKF_EINVAL on the global path.
+ */
+int letkf_set_domain_mask(letkf_ctx* ctx, const unsigned char* active);
+
 /* letkf_destroy: release everything; NULL is accepted.  Synchronises the stream. */
 int letkf_destroy(letkf_ctx* ctx);
 

@@ -118,6 +118,7 @@ _SIGS = {
     "letkf_domain_tables": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(letkf_domain_sizes),
                                            _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "letkf_set_domain_mask": (ctypes.c_int, [_VP, _VP]),
     "letkf_global_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "letkf_piston_operator": (ctypes.c_int, [ctypes.POINTER(letkf_params), _VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
@@ -304,6 +305,10 @@ def letkf_piston_operator(params: letkf_params):
     _check(load().letkf_piston_operator(ctypes.byref(params), K.ctypes.data, ctypes.byref(nd)),
            "letkf_piston_operator")
     return K
+
+
+def letkf_set_domain_mask(ctx: int, active_ptr: int) -> int:
+    return _check(load().letkf_set_domain_mask(ctx, active_ptr), "letkf_set_domain_mask")
 
 
 def letkf_global_stats(ctx: int):

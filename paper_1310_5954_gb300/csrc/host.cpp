@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.hpp"
 
 using letkf::HostModel;
@@ -353,7 +355,10 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
 namespace letkf {
 int state_bytes(const letkf_ctx* c) { return c->precision == LETKF_PREC_FP64 ? 8 : 4; }
 
+// Every stage is also an NVTX range named after it (free unless a tool such as Nsight Systems is
+// attached), whether or not the CUDA-event stage timing is on.
 void prof_begin(letkf_ctx* c, int stage) {
+    nvtxRangePushA(letkf_stage_name(stage));
     if (!c->prof_on) return;
     if (c->prof_used + 2 > c->prof_ev.size()) {
         for (int i = 0; i < 64; ++i) {
@@ -368,6 +373,7 @@ void prof_begin(letkf_ctx* c, int stage) {
 }
 
 void prof_end(letkf_ctx* c) {
+    nvtxRangePop();
     if (!c->prof_on || c->prof_used < 2) return;
     cudaEventRecord(c->prof_ev[c->prof_used - 1], c->stream);
 }
@@ -399,6 +405,38 @@ int letkf_footprint(const letkf_params* p, unsigned long long* bytes) {
     build_for(h, p);
     if (h.n_act == 0 || h.own_off.size() < 2) return LETKF_EINVAL;
     *bytes = footprint_bytes(p, h);
+    return LETKF_OK;
+}
+
+int letkf_set_domain_mask(letkf_ctx* c, const unsigned char* active) {
+    if (!c) return LETKF_EINVAL;
+    if (c->path == LETKF_PATH_GLOBAL) return LETKF_EINVAL;
+    CU(cudaSetDevice(c->device));
+    const HostModel& h = c->host;
+    const int nd = c->n_dom;
+    // observation tables with the skipped domains' ranges emptied (their actuators then keep the
+    // forecast, as a domain without observations does)
+    std::vector<int> off(nd + 1, 0), sub, cor, so(nd, 0);
+    int acc = 0;
+    for (int d = 0; d < nd; ++d) {
+        const bool on = !active || active[d] != 0;
+        if (on) {
+            sub.insert(sub.end(), h.obs_sub.begin() + h.obs_off[d], h.obs_sub.begin() + h.obs_off[d + 1]);
+            cor.insert(cor.end(), h.obs_corner.begin() + h.obs_off[d], h.obs_corner.begin() + h.obs_off[d + 1]);
+        }
+        off[d + 1] = (int)sub.size();
+        so[d] = acc;
+        acc += 2 * (off[d + 1] - off[d]);
+    }
+    // kernels of earlier frames may still read the tables
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->side) CU(cudaStreamSynchronize(c->side));
+    CU(cudaMemcpy(c->tab.obs_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!sub.empty()) {
+        CU(cudaMemcpy(c->tab.obs_sub, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(c->tab.obs_corner, cor.data(), cor.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    if (c->so_off) CU(cudaMemcpy(c->so_off, so.data(), so.size() * sizeof(int), cudaMemcpyHostToDevice));
     return LETKF_OK;
 }
 

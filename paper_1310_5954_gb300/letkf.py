@@ -140,6 +140,17 @@ class LETKF:
         """Start (True) or stop (False) stage timing; stopping returns {stage: (ms, launches)}."""
         return _lib.letkf_profile(self.ctx, 1 if enable else 0)
 
+    def set_domain_mask(self, active=None) -> None:
+        """Skip the domains whose entry of `active` (n_domains booleans) is False from the next
+        analysis on (their actuators keep the forecast); None restores every domain."""
+        if active is None:
+            _lib.letkf_set_domain_mask(self.ctx, 0)
+            return
+        a = np.ascontiguousarray(active, dtype=np.uint8)
+        if a.size != self.info.n_domains:
+            raise ValueError(f"active: expected {self.info.n_domains} entries, got {a.size}")
+        _lib.letkf_set_domain_mask(self.ctx, a.ctypes.data)
+
     def global_stats(self):
         """Global path: (Newton-Schulz steps, spectral bound s) of the last analysis."""
         return _lib.letkf_global_stats(self.ctx)
