@@ -185,6 +185,44 @@ int alloc(letkf_ctx* c, void** p, size_t bytes) {
     return LETKF_OK;
 }
 
+// Bounds of every index in the domain tables, checked on the host before anything is uploaded
+// (the kernels index with them unchecked): owned and halo actuators below n_act, observed
+// subapertures below n_subv, the four packed corners of each observed subaperture inside its
+// domain's halo list, offsets non-decreasing and ending at the list sizes, every actuator owned
+// exactly once.
+bool tables_in_bounds(const HostModel& h) {
+    const int nd = (int)h.own_off.size() - 1;
+    if (nd < 1 || (int)h.obs_off.size() != nd + 1 || (int)h.halo_off.size() != nd + 1) return false;
+    auto offsets_ok = [&](const std::vector<int>& off, size_t n) {
+        if (off.front() != 0 || (size_t)off.back() != n) return false;
+        for (int d = 0; d < nd; ++d)
+            if (off[d + 1] < off[d]) return false;
+        return true;
+    };
+    if (!offsets_ok(h.own_off, h.own.size()) || !offsets_ok(h.obs_off, h.obs_sub.size()) ||
+        !offsets_ok(h.halo_off, h.halo.size()) || h.obs_corner.size() != h.obs_sub.size())
+        return false;
+    std::vector<int> owned(h.n_act, 0);
+    for (int k : h.own) {
+        if (k < 0 || k >= h.n_act) return false;
+        owned[k] += 1;
+    }
+    for (int v : owned)
+        if (v != 1) return false;
+    for (int k : h.halo)
+        if (k < 0 || k >= h.n_act) return false;
+    for (int d = 0; d < nd; ++d) {
+        const int nh = h.halo_off[d + 1] - h.halo_off[d];
+        for (int e = h.obs_off[d]; e < h.obs_off[d + 1]; ++e) {
+            if (h.obs_sub[e] < 0 || h.obs_sub[e] >= h.n_subv) return false;
+            const unsigned pc = (unsigned)h.obs_corner[e];
+            for (int q = 0; q < 4; ++q)
+                if ((int)((pc >> (8 * q)) & 0xFFu) >= nh) return false;
+        }
+    }
+    return true;
+}
+
 // The geometry and domains of these parameters (the global path: one domain, no halo).
 void build_for(HostModel& h, const letkf_params* p) {
     if (p->path == LETKF_PATH_GLOBAL)
@@ -298,6 +336,8 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     CU(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     build_for(c->host, p);
     HostModel& h = c->host;
+    // the global path keeps one domain whose byte-packed corners it never reads
+    if (p->path != LETKF_PATH_GLOBAL && !tables_in_bounds(h)) return LETKF_EINVAL;
     c->n_act = h.n_act; c->n_subv = h.n_subv; c->n = 2 * h.n_act; c->p = 2 * h.n_subv;
     c->n_dom = (int)h.own_off.size() - 1;
     if (c->n_act == 0 || c->n_dom == 0) return LETKF_EINVAL;
@@ -464,6 +504,7 @@ int letkf_domain_tables(const letkf_params* p, letkf_domain_sizes* sz, int* own_
     build_for(h, p);
     const int nd = (int)h.own_off.size() - 1;
     if (h.n_act == 0 || nd < 1) return LETKF_EINVAL;
+    if (p->path != LETKF_PATH_GLOBAL && !tables_in_bounds(h)) return LETKF_EINVAL;
     sz->n_sub = p->n_sub;
     sz->n_act = h.n_act;
     sz->n_subv = h.n_subv;
