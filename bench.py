@@ -215,6 +215,16 @@ def peaks():
         return {}
 
 
+def _global_roofline(tflops):
+    """The global path's frame against the tensor peak (measured burst, else the fallback)."""
+    pk = peaks().get("bf16_tflops")
+    src = "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+    if not pk:
+        pk, src = 1900.0, "fallback 1.9 PFLOP/s bf16 burst, of fallback"
+    return {"bound": "tensor", "achieved": tflops, "peak": pk, "unit": "TFLOP/s", "frac": tflops / pk,
+            "peak_source": src}
+
+
 def _traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary of this kernel, or None when the
     kernel source changed since the counters were taken (the summary records its hash)."""
@@ -350,6 +360,9 @@ def global_leg(steps, warmup, flush, torch, workers=16):
             "fp32_work_gflop_per_frame": {k: v / 1e9 for k, v in work.items()},
             "fp32_work_tflops_at_p50": tot / t_med / 1e12,
             "bf16_tensor_tflops_at_p50": 3.0 * tot / t_med / 1e12,
+            # the whole frame against the tensor peak: the tensor-core work (three BF16 products
+            # per FP32 product) over the frame's p50 time
+            "roofline": _global_roofline(3.0 * tot / t_med / 1e12),
             "residual_rms": {"frames": n_fr, "burn_in": burn, "gpu": residual_rms(preds, phi, burn)},
             "device_status": status}
 

@@ -62,7 +62,7 @@ def _t(a):
 
 
 CASES = [("tiny-8x8", 20), ("tiny-8x8", 300), ("etkf-16m", None), ("etkf-16m", 600), ("vlt-40x40", 1000),
-         ("etkf-elt-m1024", None)]
+         ("etkf-elt-m1024", None), ("etkf-16m", 2048)]
 
 
 @pytest.mark.parametrize("name,m", CASES)
