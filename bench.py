@@ -242,7 +242,7 @@ def _traffic(kernel):
 def roofline(f, prof, sms, sm_max_mhz):
     """Roofline of the dominant stage (largest summed CUDA-event time over the profiled steps).
 
-    Algorithmic work of one frame (the per-unit counts stated in the design doc):
+    Algorithmic work of one frame (per-unit counts):
       dense contractions  2 m^2 (sum p_loc + sum n_loc)  (local Gram and ensemble transform)
       eigensolve / inverse square root  11 m^3 per observing domain (the dense symmetric
       eigensolver count: 9 m^3 for eigenvalues and vectors, 2 m^3 to form T)
