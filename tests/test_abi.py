@@ -64,6 +64,22 @@ def test_null_arguments(lib):
     assert lib.letkf_sync(None) == _lib.LETKF_EINVAL
     assert lib.letkf_step(None, None, 0.0, None) == _lib.LETKF_EINVAL
     assert lib.letkf_create(None, None) == _lib.LETKF_EINVAL
+    assert lib.letkf_set_domain_mask(None, None) == _lib.LETKF_EINVAL
+    n, sb = ctypes.c_int(), ctypes.c_double()
+    assert lib.letkf_global_stats(None, ctypes.byref(n), ctypes.byref(sb)) == _lib.LETKF_EINVAL
+    nd = ctypes.c_int()
+    assert lib.letkf_piston_operator(None, None, ctypes.byref(nd)) == _lib.LETKF_EINVAL
+
+
+def test_gemm_selftest_rejects_bad_shapes(lib):
+    # checked before any device call
+    assert lib.letkf_gemm_selftest(None, None, None, 1, 1, 1, 1, 64, 0, None) == _lib.LETKF_EINVAL
+    one = ctypes.c_float()
+    p = ctypes.byref(one)
+    assert lib.letkf_gemm_selftest(p, p, p, 1, 1, 1, 2, 64, 0, None) == _lib.LETKF_EINVAL     # split
+    assert lib.letkf_gemm_selftest(p, p, p, 1, 1, 1, 1, 96, 0, None) == _lib.LETKF_EINVAL     # tile width
+    assert lib.letkf_gemm_selftest(p, p, p, 1, 1, 1, 1, 128, 1, None) == _lib.LETKF_EINVAL    # MN-major wide
+    assert lib.letkf_gemm_selftest(p, p, p, 0, 1, 1, 1, 64, 0, None) == _lib.LETKF_EINVAL     # empty
 
 
 def test_footprint_on_the_host(lib):
