@@ -40,6 +40,7 @@ using namespace umma;
 constexpr int FT = 256;                  // threads per CTA
 constexpr int MT = 128;                  // MMA rows
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
+constexpr float NS_LAST = 2e-2f;   // ||I - P||_F below which the next Newton-Schulz update is the last
 constexpr int TM_G = 0, TM_P = 128, TM_Y = 256, TM_Z = 384, TM_COLS = 512;
 
 // One system's frame in a batch.  Work items item0 .. item0 + n_dom - 1 of the batch are the
@@ -507,6 +508,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
         z_in_tmem = true;
         to_mma();
+        if (rn < NS_LAST) break;     // as in the m x m form: the last update lands at the floor
     }
     if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
     tc_fence_before();
@@ -1179,6 +1181,9 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
+            // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the split-BF16
+            // rounding floor once ||I - P|| < 2e-2: the product that would confirm it is skipped
+            if (rn < NS_LAST) break;
         }
         if (!ok) break;
         if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
