@@ -40,7 +40,10 @@ using namespace umma;
 constexpr int FT = 256;                  // threads per CTA
 constexpr int MT = 128;                  // MMA rows
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
-constexpr float NS_LAST = 2e-2f;   // ||I - P||_F below which the next Newton-Schulz update is the last
+// ||I - P||_F below which the next Newton-Schulz update is the last: the update squares it
+// (~0.75 ||I - P||^2), under the split-BF16 rounding of the iteration for FP32 results, and under
+// the single-BF16 rounding of the Gram and transform (~2^-9) for mixed-precision ones.
+constexpr float NS_LAST_FP32 = 2e-2f, NS_LAST_MIXED = 1.2e-1f;
 constexpr int TM_G = 0, TM_P = 128, TM_Y = 256, TM_Z = 384, TM_COLS = 512;
 
 // One system's frame in a batch.  Work items item0 .. item0 + n_dom - 1 of the batch are the
@@ -62,6 +65,7 @@ struct SysDesc {
     int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, RA, item0;
     float inv_sigma, a, q_white;
     float a2;            // AR coefficient of the second instant (0: AR(1))
+    float ns_last;       // ||I - P||_F below which the next Newton-Schulz update is the last
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
     uint32_t frame;
@@ -508,7 +512,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
         z_in_tmem = true;
         to_mma();
-        if (rn < NS_LAST) break;     // as in the m x m form: the last update lands at the floor
+        if (rn < A.ns_last) break;     // as in the m x m form: the last update lands at the floor
     }
     if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
     tc_fence_before();
@@ -1181,9 +1185,9 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
-            // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the split-BF16
-            // rounding floor once ||I - P|| < 2e-2: the product that would confirm it is skipped
-            if (rn < NS_LAST) break;
+            // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the rounding of
+            // the result once ||I - P|| < ns_last: the product that would confirm it is skipped
+            if (rn < A.ns_last) break;
         }
         if (!ok) break;
         if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
@@ -1684,6 +1688,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->gram_terms = c->precision == LETKF_PREC_MIXED ? 1 : 3;
     S->tr_terms = 3;   // single-BF16 anomalies in the transform move the residual variance by ~2 %
     S->max_it = 40;
+    S->ns_last = c->precision == LETKF_PREC_MIXED ? NS_LAST_MIXED : NS_LAST_FP32;
     S->s_split = 8.0f;
     S->frame = (uint32_t)c->frame;
     S->off_vec = L.off_vec;
