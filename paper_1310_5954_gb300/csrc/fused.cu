@@ -44,6 +44,13 @@ constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: a wait that l
 // (~0.75 ||I - P||^2), under the split-BF16 rounding of the iteration for FP32 results, and under
 // the single-BF16 rounding of the Gram and transform (~2^-9) for mixed-precision ones.
 constexpr float NS_LAST_FP32 = 2e-2f, NS_LAST_MIXED = 1.2e-1f;
+// Newton-Schulz runs on A_s = (I + G/c)/s_ns with s_ns = s/NS_SCALE, s = 1 + ||G||_F/c: the
+// eigenvalues of A_s stay below NS_SCALE = 2.5 (||G||_F bounds the largest eigenvalue of G), inside
+// the iteration's convergence interval (0, 3), while the smallest ones start NS_SCALE times higher
+// than with s itself (||G||_F overestimates the largest eigenvalue ~3x on the ELT domains: about
+// one step fewer; low-rank G emulated no slower).  s stays the conditioning measure of the
+// precision choices.
+constexpr float NS_SCALE = 2.5f;
 constexpr int TM_G = 0, TM_P = 128, TM_Y = 256, TM_Z = 384, TM_COLS = 512;
 
 // One system's frame in a batch.  Work items item0 .. item0 + n_dom - 1 of the batch are the
@@ -441,7 +448,8 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         fro = read_fro();
     }
     const float s_scale = 1.f + sqrtf(fro) / c;
-    const float inv_cs = 1.f / (c * s_scale);
+    const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
+    const float inv_cs = 1.f / (c * s_ns);
     // ---- Z = ((I + K/c)/s)^(-1/2) by the coupled Newton-Schulz iteration (dimension P)
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {
@@ -452,7 +460,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             const int j = col0 + 8 * q8 + u;
             const bool in = row < P && j < P;
             const float id = (row == j) ? 1.f : 0.f;
-            yv[u] = in ? (id + g[u] / c) / s_scale : 0.f;
+            yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
             zv[u] = in ? id : 0.f;
         }
         if (row < NP) {
@@ -574,7 +582,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     st_times(uvp, wbar);
     // ---- (I + Z)^-1, Z = Z_ns / sqrt(s), by Newton's iteration X <- X (2I - (I + Z) X) from
     //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G
-    const float rs = rsqrtf(s_scale);
+    const float rs = rsqrtf(s_ns);
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {               // M = I + Z into Y's buffers, X_0 into T's
         float zv[8], mv[8], xv[8];
@@ -1047,7 +1055,8 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             fro = read_gram();
         }
         const float s_scale = 1.f + sqrtf(fro) / c;
-        const float inv_cs = 1.f / (c * s_scale);
+        const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
+        const float inv_cs = 1.f / (c * s_ns);
         // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
         //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
         //      Z_1 = T_0: one pass over G writes Y_0, T_0 (also as Z_1) and the residual.
@@ -1066,7 +1075,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     const int j = col0 + 8 * q8 + u;
                     const bool in = row < m && j < m;
                     const float id = (row == j) ? 1.f : 0.f;
-                    yv[u] = in ? (id + g[u] / c) / s_scale : 0.f;
+                    yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
                     const float rr = id - yv[u];
                     if (in) r2 += rr * rr;
                     tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
@@ -1277,7 +1286,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         //        arithmetic T 1 = 1 and X'_E 1 = 0, so X'_E T has zero member mean and this is
         //        x_bar 1^T + X'_E (w_bar 1^T + T); centring the product keeps the analysis mean
         //        exactly x_bar + X'_E w_bar whatever the rounding of T.
-        const float rs = rsqrtf(s_scale);
+        const float rs = rsqrtf(s_ns);
 #pragma unroll 1
         for (int q8 = 0; q8 < nq; ++q8) {
             float zv[8], bv[8];
