@@ -36,7 +36,7 @@ namespace letkf {
 
 constexpr int NS_MAX = 24;
 constexpr int NS_FLAT = 12;     // steps launched unconditionally; the rest behind one conditional node
-constexpr float NS_TOL = 1e-3f;
+constexpr float NS_TOL = 1e-2f;   // the last update then lands at ~0.75 NS_TOL^2 ~ 7.5e-5 of max |P - I|
 // device control words: run[k] (step k runs) for k = 0 .. NS_MAX, steps taken, final Z buffer
 enum { CTL_RUN = 0, CTL_STEPS = NS_MAX + 1, CTL_ZFINAL = NS_MAX + 2, CTL_N = NS_MAX + 4 };
 
