@@ -125,6 +125,12 @@ typedef struct letkf_params {
                                        a2 - a < 1 (for a2 = 0: |a| < 1) */
     int piston;                     /* letkf_piston: differential-piston removal between domains
                                        (letkf_step and the server only) */
+    int simt_q_max;                 /* fused path, m <= 127: a domain whose smaller Gram dimension
+                                       min(p_loc, m) is at most this takes an FP32 analysis on the
+                                       CUDA cores (Newton-Schulz on that q x q form) instead of
+                                       tensor-core products; 0 selects the default (32), a negative
+                                       value turns it off, at most 128.  Lowered at create time to
+                                       what shared memory holds. */
 } letkf_params;
 
 typedef struct letkf_info {
@@ -139,6 +145,9 @@ typedef struct letkf_info {
     int n_domains_observing;        /* domains with at least one observed subaperture */
     long long sum_p_loc;            /* total slopes over domains (each counted once per domain) */
     long long sum_n_loc;            /* total state rows over domains (= n) */
+    int simt_q;                     /* fused path: domains with min(p_loc, m) <= simt_q take the FP32
+                                       SIMT analysis (letkf_params.simt_q_max); 0: none */
+    int n_domains_simt;             /* observing domains that take it */
 } letkf_info;
 
 /*

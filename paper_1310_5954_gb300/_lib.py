@@ -43,6 +43,7 @@ class letkf_params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("ar2_a", ctypes.c_double),
         ("piston", ctypes.c_int),
+        ("simt_q_max", ctypes.c_int),
     ]
 
 
@@ -54,6 +55,7 @@ class letkf_info(ctypes.Structure):
         ("precision", ctypes.c_int), ("path", ctypes.c_int), ("frame", ctypes.c_ulonglong),
         ("device_bytes", ctypes.c_size_t), ("n_domains_observing", ctypes.c_int),
         ("sum_p_loc", ctypes.c_longlong), ("sum_n_loc", ctypes.c_longlong),
+        ("simt_q", ctypes.c_int), ("n_domains_simt", ctypes.c_int),
     ]
 
 

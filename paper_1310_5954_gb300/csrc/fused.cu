@@ -52,6 +52,11 @@ constexpr float NS_LAST_FP32 = 2e-2f, NS_LAST_MIXED = 1.2e-1f;
 // precision choices.
 constexpr float NS_SCALE = 2.5f;
 constexpr int TM_G = 0, TM_P = 128, TM_Y = 256, TM_Z = 384, TM_COLS = 512;
+// Domains with min(p_loc, m) at most this take the FP32 SIMT analysis by default.  Measured (mixed
+// precision, frames back to back): 8x8 pupil, m = 20, all four domains: 47.5 -> 38.4 us per frame;
+// the 16 edge domains (p_loc <= 24) of the 80x80 pupil: 199 -> 196 us; at q ~ 50 the SIMT chain is
+// slower than the tensor-core one (80x80 with the 40 domains of p_loc <= 54: 247 us).
+constexpr int SIMT_Q_DEFAULT = 32;
 
 // One system's frame in a batch.  Work items item0 .. item0 + n_dom - 1 of the batch are the
 // system's domains in its own processing order (most expensive first).
@@ -73,6 +78,7 @@ struct SysDesc {
     float inv_sigma, a, q_white;
     float a2;            // AR coefficient of the second instant (0: AR(1))
     float ns_last;       // ||I - P||_F below which the next Newton-Schulz update is the last
+    int simt_q;          // domains with min(p_loc, m) <= simt_q take the FP32 SIMT analysis (0: none)
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
     uint32_t frame;
@@ -846,6 +852,305 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     return true;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Small domains: every product in FP32 on the CUDA cores.  The Newton-Schulz iteration runs on the
+// smaller Gram form, q = min(p_loc, m), with S = Y'/sigma (p_loc x m), d the innovation / sigma and
+// c = m - 1:
+//   q = m (p_loc >= m): H = S^T S = G and Z = (I + G/c)^(-1/2) = T; w_bar = Z^2 S^T d / c;
+//   q = p_loc < m:      H = S S^T = K, the dual form of analyse_dual: w_bar = S^T u, u = Z^2 d / c,
+//                       X'_E T = X'_E - (X'_E W^T)((I + Z)^-1 W), W = Z S / sqrt(c).
+// A q x q product is q^3 FMAs over the CTA's 256 threads, against the fixed latency of a tensor-core
+// product with its TMEM read-out and BF16 split: for small q (small ensembles, the edge domains of a
+// large pupil) the SIMT chain finishes first.  The iteration, its stopping rule and the mean-weight
+// refinement are those of the tensor-core form.
+
+__host__ __device__ inline int simt_odd(int x) { return x | 1; }   // odd row strides: no bank conflicts
+                                                                   // down a column
+
+// Shared-memory floats of the SIMT analysis of a domain with p slopes and n_e analysed rows:
+// five q x q iteration matrices, S, two n_e x q products (dual form), then E = X'_E and the result,
+// which start past the AR(2) hand-over rows of the epilogue (the first n_e x m_pad floats).
+__host__ __device__ inline int simt_ws_floats(int p, int m, int m_pad, int n_e, int* off_e = nullptr) {
+    const int q = p < m ? p : m, lq = simt_odd(q), lm = simt_odd(m);
+    int off = 5 * q * lq + p * lm + 2 * n_e * lq;
+    if (off < n_e * m_pad) off = n_e * m_pad;
+    if (off_e) *off_e = off;
+    return off + 2 * n_e * lm;
+}
+
+// C = alpha A B + diag I (+ Cin), FP32; C is M x N with row stride ldc (Cin likewise, and may be C
+// itself).  Element (i, k) of A is A[i ar + k ac], (k, j) of B is B[k br + j bc].  Each thread takes
+// 2 x 2 blocks of C; the sums run over k in order.  Ends with a barrier.
+__device__ void simt_mm(float* C, int ldc, const float* A, int ar, int ac, const float* B, int br, int bc, int M,
+                        int N, int K, float alpha, float diag = 0.f, const float* Cin = nullptr) {
+    const int nbj = (N + 1) >> 1, nb = ((M + 1) >> 1) * nbj;
+    for (int t = threadIdx.x; t < nb; t += FT) {
+        const int i0 = 2 * (t / nbj), j0 = 2 * (t % nbj);
+        const int i1 = i0 + 1 < M ? i0 + 1 : i0, j1 = j0 + 1 < N ? j0 + 1 : j0;
+        const float* a0 = A + i0 * ar;
+        const float* a1 = A + i1 * ar;
+        const float* b0 = B + j0 * bc;
+        const float* b1 = B + j1 * bc;
+        float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float x0 = a0[k * ac], x1 = a1[k * ac], y0 = b0[k * br], y1 = b1[k * br];
+            c00 = fmaf(x0, y0, c00);
+            c01 = fmaf(x0, y1, c01);
+            c10 = fmaf(x1, y0, c10);
+            c11 = fmaf(x1, y1, c11);
+        }
+        const float cv[4] = {c00, c01, c10, c11};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + (u >> 1), j = j0 + (u & 1);
+            if (i < M && j < N) {
+                float r = alpha * cv[u];
+                if (i == j) r += diag;
+                if (Cin) r += Cin[i * ldc + j];
+                C[i * ldc + j] = r;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// y = alpha A x for M <= 128 rows (element (i, k) of A at A[i ar + k ac]), two threads per row; y may
+// be x.  Ends with a barrier.
+__device__ void simt_mv(float* y, const float* A, int ar, int ac, const float* x, int M, int K, float alpha,
+                        float* vtmp) {
+    const int i = threadIdx.x & 127, h = threadIdx.x >> 7;
+    float s = 0.f;
+    if (i < M)
+        for (int k = h; k < K; k += 2) s = fmaf(A[i * ar + k * ac], x[k], s);
+    vtmp[h * 128 + i] = s;
+    __syncthreads();
+    if (h == 0 && i < M) y[i] = alpha * (vtmp[i] + vtmp[128 + i]);
+    __syncthreads();
+}
+
+// Member mean of each analysed own row and its mean update X'_E w_bar (FP64 sums).
+__device__ __forceinline__ void own_row_means(const SysDesc& A, const float* XE, int n_e, const float* wbar,
+                                              float* xe_mean, float* uvec) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, m = A.m;
+    for (int e = warp; e < n_e; e += FT / 32) {
+        float sm_ = 0.f;
+        for (int i = lane; i < m; i += 32) sm_ += XE[(size_t)e * A.m_pad + i];
+        sm_ = warp_sum(sm_);
+        const float mu = sm_ / (float)m;
+        double u = 0.0;
+        for (int i = lane; i < m; i += 32) u += (double)(XE[(size_t)e * A.m_pad + i] - mu) * (double)wbar[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (lane == 0) {
+            xe_mean[e] = mu;
+            uvec[e] = (float)u;
+        }
+    }
+    __syncthreads();
+}
+
+// The SIMT analysis of domain d (halo anomalies centred in Xh, their means in xh_mean): writes
+// w_bar, xe_mean and uvec like the tensor-core form, fetches the next work item once the halo and
+// own rows are consumed, and returns the n_e x m rows of X'_E T (row stride *ld_out) in shared
+// memory.
+__device__ __noinline__ const float* analyse_simt(const FusedBatch& B, Ctrl* ctl, unsigned char* smem, int d,
+                                                  int* ld_out) {
+    const SysDesc& A = ctl->sd;
+    const int tid = threadIdx.x;
+    const int m = A.m;
+    const float c = (float)(m - 1);
+    float* vec = reinterpret_cast<float*>(smem + A.off_vec);
+    float* xh_mean = vec;
+    float* xe_mean = vec + 256;
+    float* bvec = vec + 384;
+    float* wbar = vec + 512;
+    float* vtmp = vec + 640;
+    float* vv = vec + 896;
+    float* vr = vec + 1024;
+    float* uvec = vec + 1152;
+    float* dtv = vec + 1280;
+    float* tvv = vec + 1408;
+    const float* XE = reinterpret_cast<const float*>(smem + A.off_xe);
+    const float* Xh = reinterpret_cast<const float*>(smem + A.off_xh);
+    float* ws = reinterpret_cast<float*>(smem + A.off_big);
+    const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
+    const int o0 = A.tab.obs_off[d], n_obs = A.tab.obs_off[d + 1] - o0;
+    const int p = 2 * n_obs;
+    const int n_e = (A.with_forecast && A.a2 == 0.f) ? n_own : 2 * n_own;
+    const bool dual = p < m;
+    const int q = dual ? p : m, lq = simt_odd(q), lm = simt_odd(m);
+    int off_e = 0;
+    simt_ws_floats(p, m, A.m_pad, n_e, &off_e);
+    float* Mb[5];
+    for (int t = 0; t < 5; ++t) Mb[t] = ws + t * q * lq;
+    float* S = ws + 5 * q * lq;                  // p x m, row stride lm
+    float* R1 = S + p * lm;                      // n_e x q
+    float* R2 = R1 + n_e * lq;
+    float* E = ws + off_e;                       // n_e x m: X'_E, then (dual form) X'_E T
+    float* Out = E + n_e * lm;                   // n_e x m: X'_E T (m x m form)
+
+    // ---- slopes S (k = 2 s + direction, as in the operand of the tensor-core Gram) and d / sigma
+    for (int t = tid; t < p * m; t += FT) {
+        const int k = t / m, i = t % m;
+        const int pc = A.tab.obs_corner[o0 + (k >> 1)];
+        const float a00 = Xh[(size_t)(pc & 0xFF) * A.m_pad + i];
+        const float a01 = Xh[(size_t)((pc >> 8) & 0xFF) * A.m_pad + i];
+        const float a10 = Xh[(size_t)((pc >> 16) & 0xFF) * A.m_pad + i];
+        const float a11 = Xh[(size_t)((pc >> 24) & 0xFF) * A.m_pad + i];
+        const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+        S[k * lm + i] = sl * A.inv_sigma;
+    }
+    for (int k = tid; k < p; k += FT) {
+        const int sidx = k >> 1, sub = A.tab.obs_sub[o0 + sidx];
+        const int pc = A.tab.obs_corner[o0 + sidx];
+        const float a00 = xh_mean[pc & 0xFF], a01 = xh_mean[(pc >> 8) & 0xFF];
+        const float a10 = xh_mean[(pc >> 16) & 0xFF], a11 = xh_mean[(pc >> 24) & 0xFF];
+        const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+        const float yv = (k & 1) == 0 ? A.y[sub] : A.y[A.n_subv + sub];
+        dtv[k] = (yv - sl) * A.inv_sigma;
+    }
+    __syncthreads();
+    // ---- H = S S^T (dual) or S^T S, and the scale s = 1 + ||H||_F / c
+    float* Y = Mb[0];
+    float* Z = Mb[1];
+    float* T = Mb[2];
+    float* Yn = Mb[3];
+    float* Zn = Mb[4];
+    if (dual)
+        simt_mm(Y, lq, S, lm, 1, S, 1, lm, q, q, m, 1.f);
+    else
+        simt_mm(Y, lq, S, 1, lm, S, lm, 1, q, q, p, 1.f);
+    float fr = 0.f;
+    for (int t = tid; t < q * q; t += FT) {
+        const float v = Y[(t / q) * lq + t % q];
+        fr += v * v;
+    }
+    const float fro = block_sum(ctl, fr);
+    const float s_scale = 1.f + sqrtf(fro) / c;
+    const float s_ns = s_scale / NS_SCALE;
+    const float inv_cs = 1.f / (c * s_ns);
+    // ---- coupled Newton-Schulz from Y_0 = A_s, Z_0 = I: the first step is Z_1 = T_0, Y_1 = Y_0 T_0
+    float r2 = 0.f;
+    for (int t = tid; t < q * q; t += FT) {
+        const int i = t / q, j = t % q;
+        const float id = i == j ? 1.f : 0.f;
+        const float yv = (id + Y[i * lq + j] / c) / s_ns;
+        const float rr = id - yv;
+        r2 += rr * rr;
+        Y[i * lq + j] = yv;
+        T[i * lq + j] = 1.5f * id - 0.5f * yv;
+        Z[i * lq + j] = 1.5f * id - 0.5f * yv;
+    }
+    float rn_prev = sqrtf(block_sum(ctl, r2));
+    int it = 1;
+    bool z_id = false;
+    if (rn_prev < 2e-6f * (float)q) {
+        z_id = true;     // converged at once: Z = I
+        for (int t = tid; t < q * q; t += FT) Z[(t / q) * lq + t % q] = (t / q == t % q) ? 1.f : 0.f;
+        __syncthreads();
+    } else {
+        simt_mm(Yn, lq, Y, lq, 1, T, lq, 1, q, q, q, 1.f);
+        float* sw = Y; Y = Yn; Yn = sw;
+    }
+    if (!z_id)
+        for (; it < A.max_it; ++it) {
+            simt_mm(T, lq, Z, lq, 1, Y, lq, 1, q, q, q, 1.f);        // P = Z Y
+            r2 = 0.f;
+            for (int t = tid; t < q * q; t += FT) {
+                const int i = t / q, j = t % q;
+                const float id = i == j ? 1.f : 0.f;
+                const float pv = T[i * lq + j];
+                const float rr = id - pv;
+                r2 += rr * rr;
+                T[i * lq + j] = 1.5f * id - 0.5f * pv;                // T = (3I - P) / 2
+            }
+            const float rn = sqrtf(block_sum(ctl, r2));
+            const bool conv = rn < 2e-6f * (float)q || (rn < 2e-2f && rn > 0.6f * rn_prev);
+            rn_prev = rn;
+            if (conv) break;
+            simt_mm(Yn, lq, Y, lq, 1, T, lq, 1, q, q, q, 1.f);       // Y T
+            simt_mm(Zn, lq, T, lq, 1, Z, lq, 1, q, q, q, 1.f);       // T Z
+            float* sy = Y; Y = Yn; Yn = sy;
+            float* sz = Z; Z = Zn; Zn = sz;
+            if (rn < A.ns_last) break;
+        }
+    if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
+    // ---- mean weights, refined against the exact operator
+    const int n_ref = s_scale > A.s_split ? 2 : 1;
+    if (dual) {
+        float* u = bvec;
+        simt_mv(vv, Z, lq, 1, dtv, q, q, 1.f, vtmp);
+        simt_mv(u, Z, lq, 1, vv, q, q, inv_cs, vtmp);                 // u = (cI + K)^-1 d
+        for (int ref = 0; ref < n_ref; ++ref) {
+            simt_mv(wbar, S, 1, lm, u, m, p, 1.f, vtmp);              // S^T u
+            simt_mv(tvv, S, lm, 1, wbar, p, m, 1.f, vtmp);            // K u, from the FP32 slopes
+            if (tid < p) tvv[tid] = dtv[tid] - c * u[tid] - tvv[tid];
+            __syncthreads();
+            simt_mv(vr, Z, lq, 1, tvv, q, q, 1.f, vtmp);
+            simt_mv(vv, Z, lq, 1, vr, q, q, inv_cs, vtmp);
+            if (tid < p) u[tid] += vv[tid];
+            __syncthreads();
+        }
+        simt_mv(wbar, S, 1, lm, u, m, p, 1.f, vtmp);                  // w_bar = S^T u
+    } else {
+        simt_mv(bvec, S, 1, lm, dtv, m, p, 1.f, vtmp);                // b = S^T d
+        simt_mv(vv, Z, lq, 1, bvec, q, q, 1.f, vtmp);
+        simt_mv(wbar, Z, lq, 1, vv, q, q, inv_cs, vtmp);
+        for (int ref = 0; ref < n_ref; ++ref) {
+            simt_mv(tvv, S, lm, 1, wbar, p, m, 1.f, vtmp);            // S w_bar
+            if (tid < p) tvv[tid] = dtv[tid] - tvv[tid];
+            __syncthreads();
+            simt_mv(vr, S, 1, lm, tvv, m, p, 1.f, vtmp);              // S^T (d - S w_bar)
+            if (tid < m) vr[tid] -= c * wbar[tid];
+            __syncthreads();
+            simt_mv(vv, Z, lq, 1, vr, q, q, 1.f, vtmp);
+            simt_mv(vr, Z, lq, 1, vv, q, q, inv_cs, vtmp);
+            if (tid < m) wbar[tid] += vr[tid];
+            __syncthreads();
+        }
+    }
+    // ---- own rows: means, mean update, centred anomalies X'_E; then the next item's loads
+    own_row_means(A, XE, n_e, wbar, xe_mean, uvec);
+    for (int t = tid; t < n_e * m; t += FT) {
+        const int e = t / m, i = t % m;
+        E[e * lm + i] = XE[(size_t)e * A.m_pad + i] - xe_mean[e];
+    }
+    __syncthreads();
+    if (tid == 0) fetch_item(B, ctl, smem, A.off_big);
+    // ---- transform
+    const float rs = rsqrtf(s_ns);    // T = Z / sqrt(s_ns) (m x m form); Z / sqrt(s_ns) = (I + K/c)^(-1/2)
+    *ld_out = lm;
+    if (!dual) {
+        simt_mm(Out, lm, E, lm, 1, Z, lq, 1, n_e, m, m, rs);
+        return Out;
+    }
+    // (I + Zt)^-1 with Zt = rs Z by Newton's iteration from 2/3 I (eigenvalues of I + Zt in (1, 2]):
+    // the first step is elementwise, X_1 = 4/3 I - 4/9 (I + Zt); three more leave (1/3)^16
+    float* Mi = Y;
+    float* X = T;
+    float* Q = Yn;
+    float* Xn = Zn;
+    for (int t = tid; t < q * q; t += FT) {
+        const int i = t / q, j = t % q;
+        const float mv = (i == j ? 1.f : 0.f) + rs * Z[i * lq + j];
+        Mi[i * lq + j] = mv;
+        X[i * lq + j] = (i == j ? 4.f / 3.f : 0.f) - (4.f / 9.f) * mv;
+    }
+    __syncthreads();
+    for (int k = 0; k < 3; ++k) {
+        simt_mm(Q, lq, Mi, lq, 1, X, lq, 1, q, q, q, -1.f, 2.f);     // 2I - (I + Zt) X
+        simt_mm(Xn, lq, X, lq, 1, Q, lq, 1, q, q, q, 1.f);
+        float* sx = X; X = Xn; Xn = sx;
+    }
+    simt_mm(R1, lq, E, lm, 1, S, 1, lm, n_e, q, m, 1.f);              // X'_E S^T
+    simt_mm(R2, lq, R1, lq, 1, Z, lq, 1, n_e, q, q, rs);              // X'_E W^T sqrt(c)
+    simt_mm(R1, lq, R2, lq, 1, X, lq, 1, n_e, q, q, 1.f);             // ... (I + Zt)^-1
+    simt_mm(R2, lq, R1, lq, 1, Z, lq, 1, n_e, q, q, rs / c);          // ... Zt / c
+    simt_mm(E, lm, R2, lq, 1, S, lm, 1, n_e, m, q, -1.f, 0.f, E);    // X'_E - (...) S
+    return E;
+}
+
 __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ FusedBatch B) {
     extern __shared__ __align__(1024) unsigned char smem[];
     Ctrl* ctl = reinterpret_cast<Ctrl*>(smem);
@@ -978,366 +1283,371 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             if (lane == 0) xh_mean[j] = mu;
         }
         __syncthreads();
-        for (int t = tid; t < NP * (KP >> 3); t += FT) {
-            const int i = t % NP, kc = t / NP;
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int sidx = 4 * kc + u;
-                float sx = 0.f, sy = 0.f;
-                if (i <= m && sidx < n_obs) {
-                    const int pc = A.tab.obs_corner[o0 + sidx];
-                    const int c00 = pc & 0xFF, c01 = (pc >> 8) & 0xFF, c10 = (pc >> 16) & 0xFF, c11 = (pc >> 24) & 0xFF;
-                    float a00, a01, a10, a11;
-                    if (i < m) {
-                        a00 = Xh[(size_t)c00 * A.m_pad + i]; a01 = Xh[(size_t)c01 * A.m_pad + i];
-                        a10 = Xh[(size_t)c10 * A.m_pad + i]; a11 = Xh[(size_t)c11 * A.m_pad + i];
-                    } else {
-                        a00 = xh_mean[c00]; a01 = xh_mean[c01]; a10 = xh_mean[c10]; a11 = xh_mean[c11];
-                    }
-                    sx = 0.5f * ((a01 + a11) - (a00 + a10));
-                    sy = 0.5f * ((a10 + a11) - (a00 + a01));
-                    if (i < m) {
-                        sx *= A.inv_sigma;
-                        sy *= A.inv_sigma;
-                    } else {
-                        const int sub = A.tab.obs_sub[o0 + sidx];
-                        sx = (A.y[sub] - sx) * A.inv_sigma;
-                        sy = (A.y[A.n_subv + sub] - sy) * A.inv_sigma;
-                        dtv[2 * sidx] = sx;
-                        dtv[2 * sidx + 1] = sy;
-                    }
-                }
-                v[2 * u] = sx;
-                v[2 * u + 1] = sy;
-            }
-            store8(opg_h, opg_l, i, kc * 8, KP, v, true);
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, A.gram_terms, 0);
-            mma_commit(&ctl->bar_mma);
-        }
-        if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
-        ph_mma ^= 1;
-        tc_fence_after();
-        // ---- 3a. G and b; scale s = 1 + ||G||_F / c, an upper bound of cond((m-1)I + G)
-        auto read_gram = [&]() -> float {
-            float fr = 0.f;
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float g[8];
-                tmem_ld8(tl + TM_G + 8 * q8, g);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = col0 + 8 * q8 + u;
-                    if (row < m && j < m) fr += g[u] * g[u];
-                    if (row < m && j == m) bvec[row] = g[u];
-                }
-            }
-            return block_sum(ctl, fr);
-        };
-        float fro = read_gram();
-        if (A.gram_terms < 3 && 1.f + sqrtf(fro) / c > A.s_split) {
-            // conditioning bound too large for single BF16 operands: add the high/low cross terms
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, 3, 0, 1);
-                mma_commit(&ctl->bar_mma);
-            }
-            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
-            ph_mma ^= 1;
-            tc_fence_after();
-            fro = read_gram();
-        }
-        const float s_scale = 1.f + sqrtf(fro) / c;
-        const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
-        const float inv_cs = 1.f / (c * s_ns);
-        // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
-        //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
-        //      Z_1 = T_0: one pass over G writes Y_0, T_0 (also as Z_1) and the residual.
-        int z_state = 1;     // where Z is: 0 identity, 1 shared memory only (Z_1 = T_0), 2 also TMEM
-        int it = 1;
-        bool ok = true;
-        float rn_prev;
-        {
-            float r2 = 0.f;
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float g[8], yv[8], tv[8];
-                tmem_ld8(tl + TM_G + 8 * q8, g);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = col0 + 8 * q8 + u;
-                    const bool in = row < m && j < m;
-                    const float id = (row == j) ? 1.f : 0.f;
-                    yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
-                    const float rr = id - yv[u];
-                    if (in) r2 += rr * rr;
-                    tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
-                }
-                if (row < NP) {
-                    store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                    store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
-                    store8(Zh, Zl, row, col0 + 8 * q8, NP, tv, true);
-                }
-            }
-            rn_prev = sqrtf(block_sum(ctl, r2));
-        }
-        if (rn_prev < 2e-6f * (float)m) {
-            z_state = 0;     // converged at once: Z = I
-            it = 0;
+        // ---- small domains: the FP32 SIMT analysis leaves X'_E T in shared memory
+        const bool simt = A.simt_q > 0 && min(p_loc, m) <= A.simt_q;
+        const float* sout = nullptr;
+        int sld = 0;
+        if (simt) {
+            sout = analyse_simt(B, ctl, smem, d, &sld);
         } else {
+            for (int t = tid; t < NP * (KP >> 3); t += FT) {
+                const int i = t % NP, kc = t / NP;
+                float v[8];
+    #pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int sidx = 4 * kc + u;
+                    float sx = 0.f, sy = 0.f;
+                    if (i <= m && sidx < n_obs) {
+                        const int pc = A.tab.obs_corner[o0 + sidx];
+                        const int c00 = pc & 0xFF, c01 = (pc >> 8) & 0xFF, c10 = (pc >> 16) & 0xFF, c11 = (pc >> 24) & 0xFF;
+                        float a00, a01, a10, a11;
+                        if (i < m) {
+                            a00 = Xh[(size_t)c00 * A.m_pad + i]; a01 = Xh[(size_t)c01 * A.m_pad + i];
+                            a10 = Xh[(size_t)c10 * A.m_pad + i]; a11 = Xh[(size_t)c11 * A.m_pad + i];
+                        } else {
+                            a00 = xh_mean[c00]; a01 = xh_mean[c01]; a10 = xh_mean[c10]; a11 = xh_mean[c11];
+                        }
+                        sx = 0.5f * ((a01 + a11) - (a00 + a10));
+                        sy = 0.5f * ((a10 + a11) - (a00 + a01));
+                        if (i < m) {
+                            sx *= A.inv_sigma;
+                            sy *= A.inv_sigma;
+                        } else {
+                            const int sub = A.tab.obs_sub[o0 + sidx];
+                            sx = (A.y[sub] - sx) * A.inv_sigma;
+                            sy = (A.y[A.n_subv + sub] - sy) * A.inv_sigma;
+                            dtv[2 * sidx] = sx;
+                            dtv[2 * sidx + 1] = sy;
+                        }
+                    }
+                    v[2 * u] = sx;
+                    v[2 * u + 1] = sy;
+                }
+                store8(opg_h, opg_l, i, kc * 8, KP, v, true);
+            }
             fence_async_smem();
-            tc_fence_before();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
+                issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, A.gram_terms, 0);
                 mma_commit(&ctl->bar_mma);
             }
             if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
             ph_mma ^= 1;
             tc_fence_after();
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float yv[8];
-                tmem_ld8(tl + TM_Y + 8 * q8, yv);
-                if (row < NP) store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-        }
-        if (z_state != 0)
-        for (; it < A.max_it; ++it) {
-            if (tid == 0) {
-                tc_fence_after();
-                issue_product(tbase + TM_P, Zh, Zl, Yh, Yl, NP, NP, 3, 1);
-                mma_commit(&ctl->bar_mma);
-            }
-            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) { ok = false; break; }
-            ph_mma ^= 1;
-            tc_fence_after();
-            float r2 = 0.f;
-            {   // the next chunk's TMEM load is in flight while this one is processed
-                uint32_t rc[8], rn[8];
-                tmem_ld8_async(tl + TM_P, rc);
-                tmem_wait_ld(rc);
-#pragma unroll 1
+            // ---- 3a. G and b; scale s = 1 + ||G||_F / c, an upper bound of cond((m-1)I + G)
+            auto read_gram = [&]() -> float {
+                float fr = 0.f;
+    #pragma unroll 1
                 for (int q8 = 0; q8 < nq; ++q8) {
-                    if (q8 + 1 < nq) tmem_ld8_async(tl + TM_P + 8 * (q8 + 1), rn);
-                    float tv[8];
-#pragma unroll
+                    float g[8];
+                    tmem_ld8(tl + TM_G + 8 * q8, g);
+    #pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = col0 + 8 * q8 + u;
+                        if (row < m && j < m) fr += g[u] * g[u];
+                        if (row < m && j == m) bvec[row] = g[u];
+                    }
+                }
+                return block_sum(ctl, fr);
+            };
+            float fro = read_gram();
+            if (A.gram_terms < 3 && 1.f + sqrtf(fro) / c > A.s_split) {
+                // conditioning bound too large for single BF16 operands: add the high/low cross terms
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, 3, 0, 1);
+                    mma_commit(&ctl->bar_mma);
+                }
+                if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
+                ph_mma ^= 1;
+                tc_fence_after();
+                fro = read_gram();
+            }
+            const float s_scale = 1.f + sqrtf(fro) / c;
+            const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
+            const float inv_cs = 1.f / (c * s_ns);
+            // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
+            //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
+            //      Z_1 = T_0: one pass over G writes Y_0, T_0 (also as Z_1) and the residual.
+            int z_state = 1;     // where Z is: 0 identity, 1 shared memory only (Z_1 = T_0), 2 also TMEM
+            int it = 1;
+            bool ok = true;
+            float rn_prev;
+            {
+                float r2 = 0.f;
+    #pragma unroll 1
+                for (int q8 = 0; q8 < nq; ++q8) {
+                    float g[8], yv[8], tv[8];
+                    tmem_ld8(tl + TM_G + 8 * q8, g);
+    #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int j = col0 + 8 * q8 + u;
                         const bool in = row < m && j < m;
                         const float id = (row == j) ? 1.f : 0.f;
-                        const float pv = __uint_as_float(rc[u]);
-                        const float rr = id - pv;
+                        yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
+                        const float rr = id - yv[u];
                         if (in) r2 += rr * rr;
-                        tv[u] = in ? 1.5f * id - 0.5f * pv : 0.f;
+                        tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
                     }
-                    if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
-                    if (q8 + 1 < nq) {
-                        tmem_wait_ld(rn);
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) rc[u] = rn[u];
+                    if (row < NP) {
+                        store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                        store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
+                        store8(Zh, Zl, row, col0 + 8 * q8, NP, tv, true);
                     }
                 }
+                rn_prev = sqrtf(block_sum(ctl, r2));
             }
-            r2 = block_sum(ctl, r2);
-            const float rn = sqrtf(r2);
-            const bool conv = rn < 2e-6f * (float)m || (rn < 2e-2f && rn > 0.6f * rn_prev);
-            rn_prev = rn;
-            if (conv) break;
+            if (rn_prev < 2e-6f * (float)m) {
+                z_state = 0;     // converged at once: Z = I
+                it = 0;
+            } else {
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
+                    mma_commit(&ctl->bar_mma);
+                }
+                if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
+                ph_mma ^= 1;
+                tc_fence_after();
+    #pragma unroll 1
+                for (int q8 = 0; q8 < nq; ++q8) {
+                    float yv[8];
+                    tmem_ld8(tl + TM_Y + 8 * q8, yv);
+                    if (row < NP) store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+            }
+            if (z_state != 0)
+            for (; it < A.max_it; ++it) {
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_product(tbase + TM_P, Zh, Zl, Yh, Yl, NP, NP, 3, 1);
+                    mma_commit(&ctl->bar_mma);
+                }
+                if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) { ok = false; break; }
+                ph_mma ^= 1;
+                tc_fence_after();
+                float r2 = 0.f;
+                {   // the next chunk's TMEM load is in flight while this one is processed
+                    uint32_t rc[8], rn[8];
+                    tmem_ld8_async(tl + TM_P, rc);
+                    tmem_wait_ld(rc);
+    #pragma unroll 1
+                    for (int q8 = 0; q8 < nq; ++q8) {
+                        if (q8 + 1 < nq) tmem_ld8_async(tl + TM_P + 8 * (q8 + 1), rn);
+                        float tv[8];
+    #pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = col0 + 8 * q8 + u;
+                            const bool in = row < m && j < m;
+                            const float id = (row == j) ? 1.f : 0.f;
+                            const float pv = __uint_as_float(rc[u]);
+                            const float rr = id - pv;
+                            if (in) r2 += rr * rr;
+                            tv[u] = in ? 1.5f * id - 0.5f * pv : 0.f;
+                        }
+                        if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
+                        if (q8 + 1 < nq) {
+                            tmem_wait_ld(rn);
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u) rc[u] = rn[u];
+                        }
+                    }
+                }
+                r2 = block_sum(ctl, r2);
+                const float rn = sqrtf(r2);
+                const bool conv = rn < 2e-6f * (float)m || (rn < 2e-2f && rn > 0.6f * rn_prev);
+                rn_prev = rn;
+                if (conv) break;
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                // the two products are issued by threads of different warps, so their issue loops
+                // (one tcgen05.mma per K step and BF16 term) overlap
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
+                    mma_commit(&ctl->bar_mma);
+                } else if (tid == 32) {
+                    tc_fence_after();
+                    issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
+                    mma_commit(&ctl->bar_mma2);
+                }
+                if (!wait_all2(ctl, ph_mma, ph_mma2, A.status)) { ok = false; break; }
+                ph_mma ^= 1;
+                ph_mma2 ^= 1;
+                tc_fence_after();
+    #pragma unroll 1
+                for (int q8 = 0; q8 < nq; ++q8) {
+                    uint32_t ry[8], rz[8];
+                    tmem_ld8_async(tl + TM_Y + 8 * q8, ry);
+                    tmem_ld8_async(tl + TM_Z + 8 * q8, rz);
+                    tmem_wait_ld(ry, rz);
+                    float yv[8], zv[8];
+    #pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        yv[u] = __uint_as_float(ry[u]);
+                        zv[u] = __uint_as_float(rz[u]);
+                    }
+                    if (row < NP) {
+                        store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                        store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
+                    }
+                }
+                z_state = 2;
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the rounding of
+                // the result once ||I - P|| < ns_last: the product that would confirm it is skipped
+                if (rn < A.ns_last) break;
+            }
+            if (!ok) break;
+            if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            // ---- 4. mean weights w_bar = Z (Z b) / (c s), refined against the exact operator
+            // 8 columns of this thread's half-row of Z = A_s^(-1/2)
+            auto zrow = [&](int q8, float (&zv)[8]) {
+                if (z_state == 2) {
+                    tmem_ld8(tl + TM_Z + 8 * q8, zv);
+                } else if (z_state == 1) {     // high + low BF16 parts of the shared-memory operand
+                    const uint32_t off = op_offset(row < NP ? row : 0, col0 + 8 * q8, NP);
+                    const uint4 h = *reinterpret_cast<const uint4*>(Zh + off);
+                    const uint4 l = *reinterpret_cast<const uint4*>(Zl + off);
+                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[u]));
+                        const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&lw[u]));
+                        zv[2 * u] = row < NP ? fh.x + fl.x : 0.f;
+                        zv[2 * u + 1] = row < NP ? fh.y + fl.y : 0.f;
+                    }
+                } else {
+    #pragma unroll
+                    for (int u = 0; u < 8; ++u) zv[u] = (row == col0 + 8 * q8 + u && row < m) ? 1.f : 0.f;
+                }
+            };
+            // y_out[row] = sum_j Z[row][j] x_in[j]  (all rows; rows >= m give 0)
+            auto zmatvec = [&](const float* x_in, float* y_out) {
+                float part = 0.f;
+    #pragma unroll 1
+                for (int q8 = 0; q8 < nq; ++q8) {
+                    float zv[8];
+                    zrow(q8, zv);
+    #pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (col0 + 8 * q8 + u < m) part += zv[u] * x_in[col0 + 8 * q8 + u];
+                }
+                vtmp[hh * 128 + row] = part;
+                __syncthreads();
+                if (hh == 0) y_out[row] = (row < m) ? vtmp[row] + vtmp[128 + row] : 0.f;
+                __syncthreads();
+            };
+            zmatvec(bvec, vv);
+            zmatvec(vv, wbar);
+            if (hh == 0) wbar[row] = row < m ? wbar[row] * inv_cs : 0.f;
+            __syncthreads();
+            // Refinement: r = S^T (d/sigma - S w_bar) - (m-1) w_bar with the FP32 slopes S recomputed
+            // from the halo anomalies in shared memory, so the mean weights do not inherit the
+            // rounding of the tensor-core Gram (two steps when the conditioning bound is large).
+            auto slope_at = [&](int k, int i) -> float {
+                const int sidx = k >> 1;
+                const int pc = A.tab.obs_corner[o0 + sidx];
+                const float a00 = Xh[(size_t)(pc & 0xFF) * A.m_pad + i];
+                const float a01 = Xh[(size_t)((pc >> 8) & 0xFF) * A.m_pad + i];
+                const float a10 = Xh[(size_t)((pc >> 16) & 0xFF) * A.m_pad + i];
+                const float a11 = Xh[(size_t)((pc >> 24) & 0xFF) * A.m_pad + i];
+                const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+                return sl * A.inv_sigma;
+            };
+            const int n_ref = s_scale > A.s_split ? 2 : 1;
+            for (int ref = 0; ref < n_ref; ++ref) {
+                for (int k = warp; k < p_loc; k += FT / 32) {     // t = d/sigma - S w_bar, per slope
+                    float part = 0.f;
+                    for (int i = lane; i < m; i += 32) part += slope_at(k, i) * wbar[i];
+                    part = warp_sum(part);
+                    if (lane == 0) tvv[k] = dtv[k] - part;
+                }
+                __syncthreads();
+                {                                                   // r = S^T t - (m-1) w_bar, per member
+                    const int i = tid & 127, kh = tid >> 7;
+                    float part = 0.f;
+                    if (i < m)
+                        for (int k = kh; k < p_loc; k += 2) part += slope_at(k, i) * tvv[k];
+                    vtmp[kh * 128 + i] = part;
+                    __syncthreads();
+                    if (kh == 0) vv[i] = i < m ? vtmp[i] + vtmp[128 + i] - c * wbar[i] : 0.f;
+                    __syncthreads();
+                }
+                zmatvec(vv, vr);             // Z r
+                zmatvec(vr, vv);             // Z (Z r)
+                if (hh == 0 && row < m) wbar[row] += vv[row] * inv_cs;
+                __syncthreads();
+            }
+            // ---- 5. transform: X_a[E] = x_bar 1^T + (X'_E w_bar) 1^T + centred(X'_E T).  In exact
+            //        arithmetic T 1 = 1 and X'_E 1 = 0, so X'_E T has zero member mean and this is
+            //        x_bar 1^T + X'_E (w_bar 1^T + T); centring the product keeps the analysis mean
+            //        exactly x_bar + X'_E w_bar whatever the rounding of T.
+            const float rs = rsqrtf(s_ns);
+    #pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float zv[8], bv[8];
+                zrow(q8, zv);
+    #pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = col0 + 8 * q8 + u;
+                    bv[u] = (row < m && j < m) ? zv[u] * rs : 0.f;
+                }
+                if (row < NP) store8(Bh, Bl, row, col0 + 8 * q8, NP, bv, A.tr_terms > 1);
+            }
+            own_row_means(A, XE, n_e, wbar, xe_mean, uvec);   // member means, mean update X'_E w_bar
+            const int RA = A.RA;
+            for (int t = tid; t < RA * (NP >> 3); t += FT) {
+                const int e = t % RA, kc = t / RA;
+                float v[8];
+    #pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = kc * 8 + u;
+                    v[u] = (e < n_e && k < m) ? XE[(size_t)e * A.m_pad + k] - xe_mean[e] : 0.f;
+                }
+                store8(Ah, Al, e, kc * 8, NP, v, A.tr_terms > 1);
+            }
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
-            // the two products are issued by threads of different warps, so their issue loops
-            // (one tcgen05.mma per K step and BF16 term) overlap
             if (tid == 0) {
                 tc_fence_after();
-                issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
+                issue_product(tbase + TM_P, Ah, Al, Bh, Bl, NP, NP, A.tr_terms, 1);   // X'_E T
                 mma_commit(&ctl->bar_mma);
-            } else if (tid == 32) {
-                tc_fence_after();
-                issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
-                mma_commit(&ctl->bar_mma2);
+                // the halo and own-row tiles are free now: fetch the next domain's under this product
+                fetch_item(B, ctl, smem, A.off_big);
             }
-            if (!wait_all2(ctl, ph_mma, ph_mma2, A.status)) { ok = false; break; }
+            if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
             ph_mma ^= 1;
-            ph_mma2 ^= 1;
             tc_fence_after();
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                uint32_t ry[8], rz[8];
-                tmem_ld8_async(tl + TM_Y + 8 * q8, ry);
-                tmem_ld8_async(tl + TM_Z + 8 * q8, rz);
-                tmem_wait_ld(ry, rz);
-                float yv[8], zv[8];
+        }
+        // ---- epilogue: analysis rows, forecast, prediction
+        auto prow = [&](int q8, float (&dv)[8]) {   // 8 columns of this thread's row of X'_E T
+            if (simt) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    yv[u] = __uint_as_float(ry[u]);
-                    zv[u] = __uint_as_float(rz[u]);
-                }
-                if (row < NP) {
-                    store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                    store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
-                }
-            }
-            z_state = 2;
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the rounding of
-            // the result once ||I - P|| < ns_last: the product that would confirm it is skipped
-            if (rn < A.ns_last) break;
-        }
-        if (!ok) break;
-        if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // ---- 4. mean weights w_bar = Z (Z b) / (c s), refined against the exact operator
-        // 8 columns of this thread's half-row of Z = A_s^(-1/2)
-        auto zrow = [&](int q8, float (&zv)[8]) {
-            if (z_state == 2) {
-                tmem_ld8(tl + TM_Z + 8 * q8, zv);
-            } else if (z_state == 1) {     // high + low BF16 parts of the shared-memory operand
-                const uint32_t off = op_offset(row < NP ? row : 0, col0 + 8 * q8, NP);
-                const uint4 h = *reinterpret_cast<const uint4*>(Zh + off);
-                const uint4 l = *reinterpret_cast<const uint4*>(Zl + off);
-                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[u]));
-                    const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&lw[u]));
-                    zv[2 * u] = row < NP ? fh.x + fl.x : 0.f;
-                    zv[2 * u + 1] = row < NP ? fh.y + fl.y : 0.f;
+                    const int j = col0 + 8 * q8 + u;
+                    dv[u] = (row < n_e && j < m) ? sout[row * sld + j] : 0.f;
                 }
             } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) zv[u] = (row == col0 + 8 * q8 + u && row < m) ? 1.f : 0.f;
+                tmem_ld8(tl + TM_P + 8 * q8, dv);
             }
         };
-        // y_out[row] = sum_j Z[row][j] x_in[j]  (all rows; rows >= m give 0)
-        auto zmatvec = [&](const float* x_in, float* y_out) {
-            float part = 0.f;
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float zv[8];
-                zrow(q8, zv);
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (col0 + 8 * q8 + u < m) part += zv[u] * x_in[col0 + 8 * q8 + u];
-            }
-            vtmp[hh * 128 + row] = part;
-            __syncthreads();
-            if (hh == 0) y_out[row] = (row < m) ? vtmp[row] + vtmp[128 + row] : 0.f;
-            __syncthreads();
-        };
-        zmatvec(bvec, vv);
-        zmatvec(vv, wbar);
-        if (hh == 0) wbar[row] = row < m ? wbar[row] * inv_cs : 0.f;
-        __syncthreads();
-        // Refinement: r = S^T (d/sigma - S w_bar) - (m-1) w_bar with the FP32 slopes S recomputed
-        // from the halo anomalies in shared memory, so the mean weights do not inherit the
-        // rounding of the tensor-core Gram (two steps when the conditioning bound is large).
-        auto slope_at = [&](int k, int i) -> float {
-            const int sidx = k >> 1;
-            const int pc = A.tab.obs_corner[o0 + sidx];
-            const float a00 = Xh[(size_t)(pc & 0xFF) * A.m_pad + i];
-            const float a01 = Xh[(size_t)((pc >> 8) & 0xFF) * A.m_pad + i];
-            const float a10 = Xh[(size_t)((pc >> 16) & 0xFF) * A.m_pad + i];
-            const float a11 = Xh[(size_t)((pc >> 24) & 0xFF) * A.m_pad + i];
-            const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
-            return sl * A.inv_sigma;
-        };
-        const int n_ref = s_scale > A.s_split ? 2 : 1;
-        for (int ref = 0; ref < n_ref; ++ref) {
-            for (int k = warp; k < p_loc; k += FT / 32) {     // t = d/sigma - S w_bar, per slope
-                float part = 0.f;
-                for (int i = lane; i < m; i += 32) part += slope_at(k, i) * wbar[i];
-                part = warp_sum(part);
-                if (lane == 0) tvv[k] = dtv[k] - part;
-            }
-            __syncthreads();
-            {                                                   // r = S^T t - (m-1) w_bar, per member
-                const int i = tid & 127, kh = tid >> 7;
-                float part = 0.f;
-                if (i < m)
-                    for (int k = kh; k < p_loc; k += 2) part += slope_at(k, i) * tvv[k];
-                vtmp[kh * 128 + i] = part;
-                __syncthreads();
-                if (kh == 0) vv[i] = i < m ? vtmp[i] + vtmp[128 + i] - c * wbar[i] : 0.f;
-                __syncthreads();
-            }
-            zmatvec(vv, vr);             // Z r
-            zmatvec(vr, vv);             // Z (Z r)
-            if (hh == 0 && row < m) wbar[row] += vv[row] * inv_cs;
-            __syncthreads();
-        }
-        // ---- 5. transform: X_a[E] = x_bar 1^T + (X'_E w_bar) 1^T + centred(X'_E T).  In exact
-        //        arithmetic T 1 = 1 and X'_E 1 = 0, so X'_E T has zero member mean and this is
-        //        x_bar 1^T + X'_E (w_bar 1^T + T); centring the product keeps the analysis mean
-        //        exactly x_bar + X'_E w_bar whatever the rounding of T.
-        const float rs = rsqrtf(s_ns);
-#pragma unroll 1
-        for (int q8 = 0; q8 < nq; ++q8) {
-            float zv[8], bv[8];
-            zrow(q8, zv);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = col0 + 8 * q8 + u;
-                bv[u] = (row < m && j < m) ? zv[u] * rs : 0.f;
-            }
-            if (row < NP) store8(Bh, Bl, row, col0 + 8 * q8, NP, bv, A.tr_terms > 1);
-        }
-        for (int e = warp; e < n_e; e += FT / 32) {
-            float sm_ = 0.f;
-            for (int i = lane; i < m; i += 32) sm_ += XE[(size_t)e * A.m_pad + i];
-            sm_ = warp_sum(sm_);
-            const float mu = sm_ / (float)m;
-            double u = 0.0;    // mean update X'_E w_bar, summed in FP64
-            for (int i = lane; i < m; i += 32) u += (double)(XE[(size_t)e * A.m_pad + i] - mu) * (double)wbar[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            if (lane == 0) {
-                xe_mean[e] = mu;
-                uvec[e] = (float)u;
-            }
-        }
-        __syncthreads();
-        const int RA = A.RA;
-        for (int t = tid; t < RA * (NP >> 3); t += FT) {
-            const int e = t % RA, kc = t / RA;
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = kc * 8 + u;
-                v[u] = (e < n_e && k < m) ? XE[(size_t)e * A.m_pad + k] - xe_mean[e] : 0.f;
-            }
-            store8(Ah, Al, e, kc * 8, NP, v, A.tr_terms > 1);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_product(tbase + TM_P, Ah, Al, Bh, Bl, NP, NP, A.tr_terms, 1);   // X'_E T
-            mma_commit(&ctl->bar_mma);
-            // the halo and own-row tiles are free now: fetch the next domain's under this product
-            fetch_item(B, ctl, smem, A.off_big);
-        }
-        if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
-        ph_mma ^= 1;
-        tc_fence_after();
-        // ---- epilogue: analysis rows, forecast, prediction
         const bool mine = row < n_e;
         int grow = 0, jact = 0;
         if (mine) {
@@ -1349,7 +1659,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
 #pragma unroll 1
             for (int q8 = 0; q8 < nq; ++q8) {
                 float dv[8];
-                tmem_ld8(tl + TM_P + 8 * q8, dv);
+                prow(q8, dv);
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (col0 + 8 * q8 + u < m) part += dv[u];
@@ -1367,7 +1677,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
 #pragma unroll 1
             for (int q8 = 0; q8 < nq; ++q8) {
                 float dv[8];
-                tmem_ld8(tl + TM_P + 8 * q8, dv);
+                prow(q8, dv);
                 if (mine && row >= n_own)
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
@@ -1380,7 +1690,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
 #pragma unroll 1
         for (int q8 = 0; q8 < nq; ++q8) {
             float dv[8];
-            tmem_ld8(tl + TM_P + 8 * q8, dv);
+            prow(q8, dv);
             if (!writes) continue;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -1567,6 +1877,7 @@ FusedLayout fused_layout(const letkf_ctx* c) {
     int big = std::max(2 * L.sz_opg, std::max(6 * L.sz_op, 2 * L.sz_a + 2 * L.sz_op));
     big += (MT - std::min(L.NP, L.RA)) * std::max(L.KP, L.NP) * 2;   // rows a 128-row MMA reads past the end
     L.total = L.off_big + round_up(big, 1024);
+    if (c->simt_q > 0) L.total = std::max(L.total, L.off_big + round_up(c->simt_ws, 1024));
     return L;
 }
 
@@ -1574,6 +1885,24 @@ FusedLayout fused_layout(const letkf_ctx* c) {
 
 int fused_prepare(letkf_ctx* c) {
     const HostModel& h = c->host;
+    // the largest threshold (at most the one asked for) whose SIMT workspace fits shared memory
+    c->simt_q = c->simt_ws = 0;
+    if (!uses_dual(c->m) && c->simt_q_max >= 0) {
+        const int off_big = fused_layout(c).off_big;
+        for (int q = c->simt_q_max == 0 ? SIMT_Q_DEFAULT : c->simt_q_max; q > 0; --q) {
+            int ws = 0;
+            for (int d = 0; d < c->n_dom; ++d) {
+                const int p = 2 * (h.obs_off[d + 1] - h.obs_off[d]);
+                if (p > 0 && std::min(p, c->m) <= q)
+                    ws = std::max(ws, simt_ws_floats(p, c->m, c->m_pad, 2 * (h.own_off[d + 1] - h.own_off[d])));
+            }
+            if (off_big + round_up(4 * ws, 1024) <= 227 * 1024) {
+                c->simt_q = q;
+                c->simt_ws = 4 * ws;
+                break;
+            }
+        }
+    }
     const FusedLayout L = fused_layout(c);
     c->dual = uses_dual(c->m) ? 1 : 0;
     // at most 128 slopes per domain; m <= 127 (one tile) or, in the dual form, m <= 256
@@ -1698,6 +2027,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->tr_terms = 3;   // single-BF16 anomalies in the transform move the residual variance by ~2 %
     S->max_it = 40;
     S->ns_last = c->precision == LETKF_PREC_MIXED ? NS_LAST_MIXED : NS_LAST_FP32;
+    S->simt_q = c->simt_q;
     S->s_split = 8.0f;
     S->frame = (uint32_t)c->frame;
     S->off_vec = L.off_vec;

@@ -272,7 +272,7 @@ int validate(const letkf_params* p) {
         !(p->ar2_a - p->ar1_a < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
         p->precision < 0 || p->precision > 2 || p->path < 0 || p->path > 1 || p->q_white < 0 ||
         !(p->obstruction >= 0 && p->obstruction < 1) || p->piston < LETKF_PISTON_OFF ||
-        p->piston > LETKF_PISTON_IN_LOOP)
+        p->piston > LETKF_PISTON_IN_LOOP || p->simt_q_max > 128)
         return LETKF_EINVAL;
     if (p->precision == LETKF_PREC_FP64 && p->path != LETKF_PATH_PLAIN) return LETKF_EINVAL;
     if (p->precision == LETKF_PREC_MIXED && p->path != LETKF_PATH_FUSED) return LETKF_EINVAL;
@@ -328,6 +328,7 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     c->n_sub = p->n_sub; c->m = p->m; c->dom_sub = p->dom_sub; c->halo = p->halo;
     c->precision = p->precision; c->path = p->path; c->obs_block = p->obs_block; c->device = p->device;
     c->piston = p->piston;
+    c->simt_q_max = p->simt_q_max;
     c->a = p->ar1_a; c->a2 = p->ar2_a; c->sigma = p->sigma; c->q_white = p->q_white; c->seed = p->seed;
     c->stream = (cudaStream_t)p->stream;
     const int eb = c->precision == LETKF_PREC_FP64 ? 8 : 4;
@@ -545,9 +546,12 @@ int letkf_get_info(const letkf_ctx* c, letkf_info* o) {
     o->n_domains_observing = 0;
     o->sum_p_loc = 0;
     o->sum_n_loc = 0;
+    o->simt_q = c->simt_q;
+    o->n_domains_simt = 0;
     for (int d = 0; d < c->n_dom; ++d) {
         const int no = c->host.obs_off[d + 1] - c->host.obs_off[d];
         if (no > 0) o->n_domains_observing += 1;
+        if (no > 0 && std::min(2 * no, c->m) <= c->simt_q) o->n_domains_simt += 1;
         o->sum_p_loc += 2 * no;
         o->sum_n_loc += 2 * (c->host.own_off[d + 1] - c->host.own_off[d]);
     }

@@ -124,6 +124,8 @@ struct letkf_ctx {
     // differential-piston removal: per-domain entries of the boundary subapertures, the
     // least-squares operator K (n_dom x n_dom), per-domain residual sums and the raw prediction
     int piston = 0;
+    int simt_q_max = 0;             // requested SIMT threshold (letkf_params.simt_q_max)
+    int simt_q = 0, simt_ws = 0;    // fused path: the threshold in use and its workspace bytes
     void* pst_ent = nullptr;
     int* pst_off = nullptr;
     int pst_n_ent = 0;

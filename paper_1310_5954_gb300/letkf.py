@@ -25,7 +25,7 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
                 obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
                 q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0, p0_sqrt: Optional[np.ndarray] = None,
                 precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1,
-                ar2_a: float = 0.0, piston: str = "off"):
+                ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0):
     """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used)."""
     p = _lib.letkf_params()
     keep = []
@@ -57,6 +57,7 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
     if piston not in _PISTON:
         raise ValueError(f"piston must be one of {sorted(_PISTON)}")
     p.piston = _PISTON[piston]
+    p.simt_q_max = int(simt_q_max)
     return p, keep
 
 
@@ -74,7 +75,7 @@ class LETKF:
                  q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0,
                  p0_sqrt: Optional[np.ndarray] = None, precision: str = "fp32", path: str = "plain",
                  seed: int = 0, obs_block: int = 1, device: Optional[int] = None, stream=None,
-                 ar2_a: float = 0.0, piston: str = "off"):
+                 ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -85,7 +86,7 @@ class LETKF:
         p, keep = make_params(n_sub=n_sub, m=m, ar1_a=ar1_a, sigma=sigma, dom_sub=dom_sub, halo=halo,
                               obstruction=obstruction, sub_valid=sub_valid, q_sqrt=q_sqrt, q_white=q_white,
                               p0_sqrt=p0_sqrt, precision=precision, path=path, seed=seed, obs_block=obs_block,
-                              ar2_a=ar2_a, piston=piston)
+                              ar2_a=ar2_a, piston=piston, simt_q_max=simt_q_max)
         self._keep = keep
         p.device = dev
         p.stream = self.stream.cuda_stream

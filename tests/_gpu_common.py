@@ -41,12 +41,12 @@ def oracle_filter(name, m=None, piston="off", **over):
                              a2=w.ar2_a, piston=piston)
 
 
-def gpu_filter(name, precision, path, m=None, piston="off", **over):
+def gpu_filter(name, precision, path, m=None, piston="off", simt_q_max=0, **over):
     from paper_1310_5954_gb300 import LETKF
     w, g, doms, L, Ls = model(name, m, **over)
     return LETKF(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
                  obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=precision, path=path,
-                 seed=w.seed, obs_block=w.obs_block, ar2_a=w.ar2_a, piston=piston)
+                 seed=w.seed, obs_block=w.obs_block, ar2_a=w.ar2_a, piston=piston, simt_q_max=simt_q_max)
 
 
 def rel(a, b):

@@ -50,7 +50,7 @@ def _params(**kw):
                                  dict(precision=_lib.LETKF_PREC_FP64, path=_lib.LETKF_PATH_FUSED),
                                  dict(precision=_lib.LETKF_PREC_MIXED, path=_lib.LETKF_PATH_PLAIN),
                                  dict(precision=_lib.LETKF_PREC_FP64, m=200), dict(dom_sub=12, halo=2),
-                                 dict(piston=3), dict(piston=-1)])
+                                 dict(piston=3), dict(piston=-1), dict(simt_q_max=129)])
 def test_create_rejects_invalid_parameters_before_touching_the_device(lib, bad):
     p = _params(**bad)
     out = ctypes.c_void_p(1234)

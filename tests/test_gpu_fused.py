@@ -30,11 +30,15 @@ def _t(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
 
 
+# simt_q_max: 0 is the default threshold (min(p_loc, m) <= 32 on the CUDA cores: all of tiny, m = 20,
+# and the edge domains of VLT and ELT), -1 puts every domain on the tensor cores, 64 also every
+# VLT domain (m = 50) and the 40 ELT domains with p_loc <= 54
+@pytest.mark.parametrize("simt", [0, -1, 64])
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
 @pytest.mark.parametrize("name,frames", [("tiny-8x8", 3), ("vlt-40x40", 2), ("elt-80x80", 2)])
-def test_single_frame_analysis(prec, name, frames):
+def test_single_frame_analysis(prec, name, frames, simt):
     y, _ = slopes(name, frames + 1)
-    f = gpu_filter(name, prec, "fused")
+    f = gpu_filter(name, prec, "fused", simt_q_max=simt)
     o = oracle_filter(name)
     tm, te = TOL[prec]
     for k in range(frames):
@@ -94,15 +98,16 @@ def test_dual_form_free_running_residual():
     f.close()
 
 
+@pytest.mark.parametrize("simt", [0, -1])
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
-def test_step_matches_oracle_free_running(prec):
+def test_step_matches_oracle_free_running(prec, simt):
     """30 free-running frames from the cold start.  The per-analysis bound (1e-4, FP32) is
     checked above from identical states; here the transform's rounding (split-BF16 Newton-
     Schulz, about 1e-4 at the first frames' condition numbers of ~5e3) also feeds the next
     frames' ensembles, so the FP32 bound is 2e-4."""
     n = 30
     y, _ = slopes("tiny-8x8", n)
-    f = gpu_filter("tiny-8x8", prec, "fused")
+    f = gpu_filter("tiny-8x8", prec, "fused", simt_q_max=simt)
     o = oracle_filter("tiny-8x8")
     tm = TOL[prec][0]
     for k in range(n):
@@ -283,9 +288,10 @@ def test_autotune_restores_the_filter_and_changes_no_result(tmp_path):
         f.close()
 
 
-@pytest.mark.parametrize("prec,path,m", [("fp32", "plain", None), ("fp32", "fused", None), ("mixed", "fused", None),
-                                         ("mixed", "fused", 150)])
-def test_ar2_model_matches_oracle(prec, path, m):
+@pytest.mark.parametrize("prec,path,m,simt", [("fp32", "plain", None, 0), ("fp32", "fused", None, 0),
+                                              ("mixed", "fused", None, 0), ("mixed", "fused", None, -1),
+                                              ("mixed", "fused", 150, 0)])
+def test_ar2_model_matches_oracle(prec, path, m, simt):
     """AR(2) turbulence model (Sect. 2.1, "AR 1 or AR 2"): A1 = [[a I, a2 I], [I, 0]] with (a, a2)
     fitted to the frozen flow; free-running predictions track the FP64 oracle.  The fitted model
     (a ~ 1.6, a2 ~ -0.65) has a companion matrix of norm ~ a + |a2| ~ 2.3 instead of 0.99, which
@@ -300,7 +306,7 @@ def test_ar2_model_matches_oracle(prec, path, m):
     over = dict(ar1_a=round(a1, 6), ar2_a=round(a2, 6))
     n = 20
     y, _ = slopes("tiny-8x8", n)
-    f = gpu_filter("tiny-8x8", prec, path, m=m, **over)
+    f = gpu_filter("tiny-8x8", prec, path, m=m, simt_q_max=simt, **over)
     o = oracle_filter("tiny-8x8", m=m, **over)
     tol = 1e-3 if prec == "fp32" else 2e-2
     worst = 0.0
@@ -309,5 +315,37 @@ def test_ar2_model_matches_oracle(prec, path, m):
         xo = o.step(y[k].astype(np.float32).astype(np.float64))
         worst = max(worst, rel(xp, xo))
     assert worst < tol, worst
+    assert f.sync() == 0
+    f.close()
+
+
+@pytest.mark.parametrize("name,m,ask,want_q,want_n", [
+    ("tiny-8x8", None, 0, 32, 4), ("vlt-40x40", None, 0, 32, 4), ("elt-80x80", None, 0, 32, 16),
+    ("vlt-40x40", None, 64, 64, 92), ("elt-80x80", None, 64, 64, 40), ("elt-80x80", None, -1, 0, 0),
+    ("elt-80x80", None, 24, 24, 16), ("elt-80x80", 150, 0, 0, 0)])
+def test_simt_threshold(name, m, ask, want_q, want_n):
+    """Which domains take the FP32 SIMT analysis: min(p_loc, m) <= the threshold; none in the
+    dual form (m >= 128)."""
+    f = gpu_filter(name, "mixed", "fused", m=m, simt_q_max=ask)
+    assert (f.info.simt_q, f.info.n_domains_simt) == (want_q, want_n)
+    f.close()
+
+
+def test_simt_threshold_lowered_to_fit_shared_memory():
+    """Asked for every ELT domain (q <= 100), the threshold drops to what shared memory holds, and
+    the analysis still matches the oracle."""
+    y, _ = slopes("elt-80x80", 2)
+    f = gpu_filter("elt-80x80", "fp32", "fused", simt_q_max=128)
+    assert 64 <= f.info.simt_q < 100
+    assert f.info.n_domains_simt >= 40
+    o = oracle_filter("elt-80x80")
+    xf = o.X.astype(np.float32).astype(np.float64)
+    f.set_state(_t(xf), 0)
+    o.X = xf.copy()
+    f.analyze(_t(y[0]))
+    o.analyze(y[0].astype(np.float32).astype(np.float64))
+    xa = f.get_state()[0].cpu().numpy().astype(np.float64)
+    assert rel(xa.mean(1), o.X.mean(1)) < TOL["fp32"][0]
+    assert rel(xa, o.X) < TOL["fp32"][1]
     assert f.sync() == 0
     f.close()
