@@ -49,6 +49,12 @@ class Workload:
     q: int = 4               # fine samples per pitch in the truth sensor
     nonstationary: bool = False
     ar2_a: float = 0.0       # AR coefficient of phi_{k-1} (0: AR(1) model)
+    # frozen-flow layers ((Cn2 fraction, speed m/s, direction rad), ...), fractions summing to 1;
+    # empty: one layer moving at (wind, wind_angle), or the non-stationary schedule
+    layers: tuple = ()
+
+    def layer_list(self):
+        return self.layers if self.layers else ((1.0, self.wind, self.wind_angle),)
 
     @property
     def pitch(self) -> float:
@@ -99,9 +105,18 @@ class Workload:
         of one phase instant at the given actuators ((n_act, 2) row, column positions)."""
         return self._chol(self._lag_gather(act_rc), jitter)
 
-    def _shift(self, frames: int = 1):
-        v, ang = self.wind_at(0)
+    def _shift(self, frames: int = 1, layer: int = 0):
+        if self.layers:
+            _, v, ang = self.layers[layer]
+        else:
+            v, ang = self.wind_at(0)
         return (frames * v / self.frame_rate * math.cos(ang), frames * v / self.frame_rate * math.sin(ang))
+
+    def _lagged_cov(self, act_rc: np.ndarray, frames: int) -> np.ndarray:
+        """Covariance between the phase at the actuators now and `frames` frames later: the sum over
+        independent layers of fraction x (von Karman covariance at r0, shifted by that layer's path);
+        a layer of fraction f has r0_l = r0 f^(-3/5), and the covariance scales as r0^(-5/3)."""
+        return sum(f * self._lag_gather(act_rc, self._shift(frames, l)) for l, (f, _, _) in enumerate(self.layer_list()))
 
     def process_noise_sqrt(self, act_rc: np.ndarray, jitter: float = 1e-8) -> np.ndarray:
         """Lower-triangular L with L L^T = Q + eps I, Q the covariance of the AR innovation
@@ -112,17 +127,17 @@ class Workload:
         (a2 = 0: the AR(1) innovation (1 + a^2) S(0) - a (S(s) + S(s)^T))."""
         a, a2 = self.ar1_a, self.ar2_a
         S0 = self._lag_gather(act_rc)
-        S1 = self._lag_gather(act_rc, self._shift(1))
+        S1 = self._lagged_cov(act_rc, 1)
         Q = (1.0 + a * a + a2 * a2) * S0 - (a - a * a2) * (S1 + S1.T)
         if a2 != 0.0:
-            S2 = self._lag_gather(act_rc, self._shift(2))
+            S2 = self._lagged_cov(act_rc, 2)
             Q = Q - a2 * (S2 + S2.T)
         return self._chol(Q, jitter)
 
     def ar2_fit(self, act_rc: np.ndarray):
         """(a, a2) of the AR(2) model fitted to the frozen-flow turbulence: the Yule-Walker
         equations on the phase autocovariance summed over the actuators, t_j = tr S(js)."""
-        t = [float(np.trace(self._lag_gather(act_rc, self._shift(j)))) for j in range(3)]
+        t = [float(np.trace(self._lagged_cov(act_rc, j))) for j in range(3)]
         return yule_walker_ar2(*t)
 
 
@@ -157,6 +172,13 @@ WORKLOADS = {
     "etkf-elt-m1024": _wl(6, name="etkf-elt-m1024", n_sub=80, obstruction=0.28, m=1024, dom_sub=80, halo=0,
                           ar1_a=0.995, sigma=0.2, tel_diam=40.0, d_over_r0=40.0, L0=25.0, wind=15.0,
                           frame_rate=1000.0, n_frames=5000),
+    # The paper's 8 m SCAO case (Sect. 3, Sect. 3.1): 16x16 Fried system (241 actuators), r0 =
+    # 0.525 m, L0 = 25 m, three frozen-flow layers (7.5, 12.5, 15 m/s; Cn2 0.5, 0.17, 0.33), 500 Hz,
+    # ten fine samples per subaperture; the layer directions are not given (0, 60, 120 degrees here).
+    "scao-8m": _wl(7, name="scao-8m", n_sub=16, obstruction=0.0, m=100, dom_sub=4, halo=2,
+                   ar1_a=0.99, sigma=0.1, tel_diam=8.0, d_over_r0=8.0 / 0.525, L0=25.0, wind=7.5,
+                   frame_rate=500.0, n_frames=2000, q=10,
+                   layers=((0.5, 7.5, 0.0), (0.17, 12.5, math.pi / 3), (0.33, 15.0, 2 * math.pi / 3))),
     # The same ELT system under a non-stationary schedule (see Workload methods).
     "elt-80x80-nonstationary": _wl(3, name="elt-80x80-nonstationary", n_sub=80, obstruction=0.28,
                                    m=100, dom_sub=4, halo=2, ar1_a=0.995, sigma=0.1, tel_diam=40.0,
@@ -202,10 +224,14 @@ class TruthStream:
         self.sensor = FineGridSensor(w.n_sub, w.q)
         dx = w.pitch / w.q
         if n_pix is None:
-            need = max(4.0 * w.L0, 2.0 * w.tel_diam + w.wind * w.n_frames / w.frame_rate)
+            vmax = max(v for _, v, _ in w.layer_list())
+            need = max(4.0 * w.L0, 2.0 * w.tel_diam + vmax * w.n_frames / w.frame_rate)
             n_pix = 1 << int(math.ceil(math.log2(max(256.0, need / dx))))
             n_pix = min(n_pix, 4096)
-        self.screen = VKScreen(n_pix, dx, w.r0, w.L0, seed=w.seed * 16 + 3)
+        # one screen per layer (r0_l = r0 f^(-3/5)); the first keeps the single-layer seed
+        self.screens = [VKScreen(n_pix, dx, w.r0 * f ** (-0.6), w.L0, seed=w.seed * 16 + 3 + 100 * l)
+                        for l, (f, _, _) in enumerate(w.layer_list())]
+        self.screen = self.screens[0]
         self.noise_seed = w.seed * 16 + 2
         self._xg, self._yg = self.sensor.fine_coords(w.pitch)
         self._shift = [(0.0, 0.0)]
@@ -222,6 +248,12 @@ class TruthStream:
     def phase_fine(self, k: int) -> np.ndarray:
         if k < 0:
             k = 0
+        if self.w.layers:
+            out = np.zeros_like(self._xg)
+            for l, scr in enumerate(self.screens):
+                sx, sy = self.w._shift(k, l)
+                out += scr.sample(self._xg + sx, self._yg + sy)
+            return out
         sx, sy = self._shift_at(k)
         return self.w.screen_scale(k) * self.screen.sample(self._xg + sx, self._yg + sy)
 
