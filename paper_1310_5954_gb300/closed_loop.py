@@ -22,6 +22,7 @@ Host-side numpy: this evaluates a control law, it is not part of the per-frame u
 from __future__ import annotations
 
 import numpy as np
+from scipy import sparse
 
 
 class DeformableMirror:
@@ -55,24 +56,36 @@ class DeformableMirror:
         ar, ac = np.nonzero(act_valid)
         self.n_pix, self.n_act = pr.size, ar.size
         ln_c = np.log(self.coupling)
-
-        def influence(r, c, rows, cols):
-            d2 = ((r[:, None] - rows[None, :]) ** 2 + (c[:, None] - cols[None, :]) ** 2).astype(np.float64)
-            f = np.exp(ln_c * d2)
-            f[d2 > reach * reach] = 0.0
-            return f
-
-        N = influence(pr / q, pc / q, ar.astype(np.float64), ac.astype(np.float64))
-        F = influence(ar.astype(np.float64), ac.astype(np.float64), ar.astype(np.float64), ac.astype(np.float64))
-        # G = N F^-1 (F symmetric positive definite: a Gaussian kernel on distinct points)
-        self.G = np.linalg.solve(F, N.T).T
+        # N (pupil pixels x actuators), sparse: each influence function within `reach` pitches
+        pix_index = -np.ones((nf, nf), dtype=np.int64)
+        pix_index[pr, pc] = np.arange(self.n_pix)
+        w = int(np.floor(reach * q))
+        rows, cols, vals = [], [], []
+        for j, (a_r, a_c) in enumerate(zip(ar, ac)):
+            r0, r1 = max(a_r * q - w, 0), min(a_r * q + w, nf - 1)
+            c0, c1 = max(a_c * q - w, 0), min(a_c * q + w, nf - 1)
+            rr, cc = np.meshgrid(np.arange(r0, r1 + 1), np.arange(c0, c1 + 1), indexing="ij")
+            d2 = ((rr / q - a_r) ** 2 + (cc / q - a_c) ** 2).ravel()
+            pi = pix_index[rr, cc].ravel()
+            keep = (pi >= 0) & (d2 <= reach * reach)
+            rows.append(pi[keep])
+            cols.append(np.full(int(keep.sum()), j))
+            vals.append(np.exp(ln_c * d2[keep]))
+        self.N = sparse.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                                   shape=(self.n_pix, self.n_act))
+        d2a = ((ar[:, None] - ar[None, :]) ** 2 + (ac[:, None] - ac[None, :]) ** 2).astype(np.float64)
+        F = np.exp(ln_c * d2a)
+        F[d2a > reach * reach] = 0.0
         self.F = F
+        # F is symmetric positive definite (a Gaussian kernel on distinct points)
+        self.F_inv = np.linalg.inv(F)
 
     def correction(self, x_act: np.ndarray) -> np.ndarray:
         """Mirror surface on the pupil pixels that passes through x_act at the actuators; x_act is
         (n_act,) or (frames, n_act)."""
         x = np.asarray(x_act, dtype=np.float64)
-        return x @ self.G.T
+        u = self.F_inv @ x.T                       # commands: F u = x
+        return np.asarray(self.N @ u).T
 
     def residual_variance(self, phi_fine: np.ndarray, x_act: np.ndarray) -> np.ndarray:
         """Piston-removed variance over the pupil of phi_fine - correction(x_act).  phi_fine:

@@ -1560,30 +1560,47 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             // Refinement: r = S^T (d/sigma - S w_bar) - (m-1) w_bar with the FP32 slopes S recomputed
             // from the halo anomalies in shared memory, so the mean weights do not inherit the
             // rounding of the tensor-core Gram (two steps when the conditioning bound is large).
-            auto slope_at = [&](int k, int i) -> float {
-                const int sidx = k >> 1;
-                const int pc = A.tab.obs_corner[o0 + sidx];
-                const float a00 = Xh[(size_t)(pc & 0xFF) * A.m_pad + i];
-                const float a01 = Xh[(size_t)((pc >> 8) & 0xFF) * A.m_pad + i];
-                const float a10 = Xh[(size_t)((pc >> 16) & 0xFF) * A.m_pad + i];
-                const float a11 = Xh[(size_t)((pc >> 24) & 0xFF) * A.m_pad + i];
-                const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
-                return sl * A.inv_sigma;
-            };
+            // S = D_loc X'_h / sigma is linear in the halo anomalies, so S w_bar is the stencil of
+            // h = X'_h w_bar and S^T t is X'_h^T applied to the stencil's transpose of t: n_h x m
+            // products instead of rebuilding every slope from its four corners
+            float* hv = vec + 1536;                  // 256: halo-actuator vector
+            int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
+            for (int s = tid; s < n_obs; s += FT) pcs[s] = A.tab.obs_corner[o0 + s];
             const int n_ref = s_scale > A.s_split ? 2 : 1;
             for (int ref = 0; ref < n_ref; ++ref) {
-                for (int k = warp; k < p_loc; k += FT / 32) {     // t = d/sigma - S w_bar, per slope
+                for (int j = warp; j < n_h; j += FT / 32) {        // h = X'_h w_bar
                     float part = 0.f;
-                    for (int i = lane; i < m; i += 32) part += slope_at(k, i) * wbar[i];
+                    for (int i = lane; i < m; i += 32) part += Xh[(size_t)j * A.m_pad + i] * wbar[i];
                     part = warp_sum(part);
-                    if (lane == 0) tvv[k] = dtv[k] - part;
+                    if (lane == 0) hv[j] = part;
                 }
                 __syncthreads();
-                {                                                   // r = S^T t - (m-1) w_bar, per member
+                for (int k = tid; k < p_loc; k += FT) {            // t = d/sigma - S w_bar, per slope
+                    const int pc = pcs[k >> 1];
+                    const float a00 = hv[pc & 0xFF], a01 = hv[(pc >> 8) & 0xFF];
+                    const float a10 = hv[(pc >> 16) & 0xFF], a11 = hv[(pc >> 24) & 0xFF];
+                    const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+                    tvv[k] = dtv[k] - sl * A.inv_sigma;
+                }
+                __syncthreads();
+                for (int j = tid; j < n_h; j += FT) {              // g = D_loc^T t / sigma, per halo actuator
+                    float g = 0.f;
+                    for (int s = 0; s < n_obs; ++s) {
+                        const int pc = pcs[s];
+                        const float tx = tvv[2 * s], ty = tvv[2 * s + 1];
+                        if ((pc & 0xFF) == j) g += -0.5f * tx - 0.5f * ty;
+                        if (((pc >> 8) & 0xFF) == j) g += 0.5f * tx - 0.5f * ty;
+                        if (((pc >> 16) & 0xFF) == j) g += -0.5f * tx + 0.5f * ty;
+                        if (((pc >> 24) & 0xFF) == j) g += 0.5f * tx + 0.5f * ty;
+                    }
+                    hv[j] = g * A.inv_sigma;
+                }
+                __syncthreads();
+                {                                                   // r = X'_h^T g - (m-1) w_bar, per member
                     const int i = tid & 127, kh = tid >> 7;
                     float part = 0.f;
                     if (i < m)
-                        for (int k = kh; k < p_loc; k += 2) part += slope_at(k, i) * tvv[k];
+                        for (int j = kh; j < n_h; j += 2) part += Xh[(size_t)j * A.m_pad + i] * hv[j];
                     vtmp[kh * 128 + i] = part;
                     __syncthreads();
                     if (kh == 0) vv[i] = i < m ? vtmp[i] + vtmp[128 + i] - c * wbar[i] : 0.f;

@@ -179,6 +179,12 @@ WORKLOADS = {
                    ar1_a=0.99, sigma=0.1, tel_diam=8.0, d_over_r0=8.0 / 0.525, L0=25.0, wind=7.5,
                    frame_rate=500.0, n_frames=2000, q=10,
                    layers=((0.5, 7.5, 0.0), (0.17, 12.5, math.pi / 3), (0.33, 15.0, 2 * math.pi / 3))),
+    # The paper's 16 m case (Sect. 3.2, Fig. 3): 32x32 unobstructed (877 actuators), the same
+    # turbulence and loop rate.
+    "scao-16m": _wl(8, name="scao-16m", n_sub=32, obstruction=0.0, m=197, dom_sub=4, halo=2,
+                    ar1_a=0.99, sigma=0.1, tel_diam=16.0, d_over_r0=16.0 / 0.525, L0=25.0, wind=7.5,
+                    frame_rate=500.0, n_frames=2000, q=10,
+                    layers=((0.5, 7.5, 0.0), (0.17, 12.5, math.pi / 3), (0.33, 15.0, 2 * math.pi / 3))),
     # The same ELT system under a non-stationary schedule (see Workload methods).
     "elt-80x80-nonstationary": _wl(3, name="elt-80x80-nonstationary", n_sub=80, obstruction=0.28,
                                    m=100, dom_sub=4, halo=2, ar1_a=0.995, sigma=0.1, tel_diam=40.0,

@@ -39,25 +39,25 @@ def _built():
 
 
 @functools.lru_cache(maxsize=None)
-def _case(sigma):
-    w = workload("scao-8m")
+def _case(sigma, name="scao-8m", n_frames=N_FRAMES):
+    w = workload(name)
     w.sigma = sigma
     g = geometry.make_geometry(w.n_sub, w.obstruction)
     L = w.process_noise_sqrt(g.act_rc)
     Ls = w.stationary_sqrt(g.act_rc)
     ts = TruthStream(w)
-    fr = ts.frames(0, N_FRAMES)
+    fr = ts.frames(0, n_frames)
     s = fr["slopes"]
     y = np.ascontiguousarray(np.concatenate([s[:, 0][:, g.sub_valid], s[:, 1][:, g.sub_valid]], axis=1))
     dm = DeformableMirror(g.sub_valid, g.act_valid, w.q)
-    phi_next = np.stack([ts.phase_fine(k + 1)[dm.pupil] for k in range(BURN, N_FRAMES)]).astype(np.float32)
+    phi_next = np.stack([ts.phase_fine(k + 1)[dm.pupil] for k in range(BURN, n_frames)]).astype(np.float32)
     # the Kalman filter on the Riccati gain, same AR(1) model and noise
     A = kf.ar1_companion(g.n_act, w.ar1_a)
     C = fried.observation_matrix(g, w.obs_block)
     H = kf.kalman_gain(kf.dare(A, C, kf.process_covariance(L), sigma ** 2 * np.eye(g.p)), C, sigma ** 2 * np.eye(g.p))
     x = np.zeros(g.n)
     kfp = []
-    for k in range(N_FRAMES):
+    for k in range(n_frames):
         x = kf.kf_predict(x, y[k], A, C, H)
         kfp.append(x[: g.n_act].copy())
     return w, g, L, Ls, y, dm, phi_next, np.array(kfp)
@@ -77,15 +77,15 @@ def _ec(case, preds):
 
 
 @functools.lru_cache(maxsize=None)
-def _run(sigma, path, m, piston="off"):
-    case = _case(sigma)
+def _run(sigma, path, m, piston="off", name="scao-8m", n_frames=N_FRAMES):
+    case = _case(sigma, name, n_frames)
     w, g, L, Ls, y, _, _, _ = case
     prec = "fp32" if path == "global" else "mixed"
     f = LETKF(n_sub=w.n_sub, m=m, ar1_a=w.ar1_a, sigma=sigma, dom_sub=w.dom_sub, halo=w.halo,
               obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=prec, path=path, seed=w.seed,
               obs_block=w.obs_block, piston=piston)
     yd = torch.as_tensor(y, dtype=torch.float32, device="cuda")
-    preds = torch.stack([f.step(yd[k]) for k in range(N_FRAMES)]).cpu().numpy()
+    preds = torch.stack([f.step(yd[k]) for k in range(n_frames)]).cpu().numpy()
     status = f.sync()
     f.close()
     ec = _ec(case, preds)
@@ -95,8 +95,9 @@ def _run(sigma, path, m, piston="off"):
     return ec
 
 
-def _loss(sigma, ec):
-    ec_kf = _ec(_case(sigma), _case(sigma)[7])
+def _loss(sigma, ec, name="scao-8m", n_frames=N_FRAMES):
+    case = _case(sigma, name, n_frames)
+    ec_kf = _ec(case, case[7])
     return (ec_kf - ec) / ec_kf
 
 
@@ -128,3 +129,21 @@ def test_local_etkf_beats_the_global_one_and_piston_removal_helps():
         assert min(out, inl) < loc, m        # removing the differential pistons lowers the loss
     assert rows[200][0] < rows[100][0]       # and the local loss falls with m
     assert rows[200][2] < rows[100][2] < in_loop_50
+
+
+def test_16m_local_etkf_with_piston_removal_within_3_percent_at_197_members():
+    """Sect. 3.2, Fig. 3 (16 m, 32x32, 877 actuators): the local ETKF does better than the global one
+    at the same ensemble size, removing the differential pistons lowers its loss, and with 197
+    members the loss against the KF falls under 3 %.  The paper reaches 3 % with a post-processing
+    method it does not describe; the least-squares correction of the output alone (the reading used
+    here) measured 6.2 %, the same correction applied inside the loop 1.1 % (sigma = 0.1)."""
+    sigma, name, n = 0.1, "scao-16m", 1000
+    case = _case(sigma, name, n)
+    ec_kf = _ec(case, case[7])
+    loss = {mode: _loss(sigma, _run(sigma, "fused", 197, mode, name, n), name, n) for mode in ("off", "output", "in_loop")}
+    glob = _loss(sigma, _run(sigma, "global", 197, "off", name, n), name, n)
+    print(f"\n16 m, sigma {sigma}: EC(KF) {ec_kf:.4f}; loss vs KF at m = 197: local {loss['off']:.4f}, "
+          f"local + piston output {loss['output']:.4f}, local + piston in loop {loss['in_loop']:.4f}, global {glob:.4f}")
+    assert loss["off"] < glob
+    assert loss["output"] < loss["off"] and loss["in_loop"] < loss["off"]
+    assert loss["in_loop"] < 0.03
