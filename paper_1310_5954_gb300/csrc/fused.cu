@@ -555,11 +555,31 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         if (hh == 0) y_out[row] = (row < P) ? vtmp[row] + vtmp[128 + row] : 0.f;
         __syncthreads();
     };
+    // S = D_loc X'_h / sigma is linear in the halo anomalies: S^T u is X'_h^T applied to the
+    // stencil's transpose of u, and S w the stencil of X'_h w (n_h x m products over the scratch
+    // instead of four scratch loads per slope and member)
+    float* hv = vec + 1536;                          // 256: halo-actuator vector
+    int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
+    for (int s = tid; s < n_obs; s += FT) pcs[s] = A.tab.obs_corner[o0 + s];
+    __syncthreads();
     auto st_times = [&](const float* u_in, float* w_out) {    // w = S^T u (members)
+        for (int j = tid; j < n_h; j += FT) {                  // g = D_loc^T u / sigma
+            float g = 0.f;
+            for (int s = 0; s < n_obs; ++s) {
+                const int pc = pcs[s];
+                const float tx = u_in[2 * s], ty = u_in[2 * s + 1];
+                if ((pc & 0xFF) == j) g += -0.5f * tx - 0.5f * ty;
+                if (((pc >> 8) & 0xFF) == j) g += 0.5f * tx - 0.5f * ty;
+                if (((pc >> 16) & 0xFF) == j) g += -0.5f * tx + 0.5f * ty;
+                if (((pc >> 24) & 0xFF) == j) g += 0.5f * tx + 0.5f * ty;
+            }
+            hv[j] = g * A.inv_sigma;
+        }
+        __syncthreads();
         for (int i = tid; i < m; i += FT) {
             float acc = 0.f;
 #pragma unroll 4
-            for (int k = 0; k < P; ++k) acc += slope_at(k, i) * u_in[k];
+            for (int j = 0; j < n_h; ++j) acc += Xs[(size_t)j * A.m_pad + i] * hv[j];
             w_out[i] = acc;
         }
         __syncthreads();
@@ -573,11 +593,19 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const int n_ref = s_scale > A.s_split ? 2 : 1;
     for (int ref = 0; ref < n_ref; ++ref) {
         st_times(uvp, wbar);                                   // S^T u
-        for (int k = warp; k < P; k += FT / 32) {              // rho = d - c u - S (S^T u)
+        for (int j = warp; j < n_h; j += FT / 32) {            // h = X'_h (S^T u)
             float part = 0.f;
-            for (int i = lane; i < m; i += 32) part += slope_at(k, i) * wbar[i];
+            for (int i = lane; i < m; i += 32) part += Xs[(size_t)j * A.m_pad + i] * wbar[i];
             part = warp_sum(part);
-            if (lane == 0) vr[k] = dvec[k] - c * uvp[k] - part;
+            if (lane == 0) hv[j] = part;
+        }
+        __syncthreads();
+        for (int k = tid; k < P; k += FT) {                    // rho = d - c u - S (S^T u)
+            const int pc = pcs[k >> 1];
+            const float a00 = hv[pc & 0xFF], a01 = hv[(pc >> 8) & 0xFF];
+            const float a10 = hv[(pc >> 16) & 0xFF], a11 = hv[(pc >> 24) & 0xFF];
+            const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
+            vr[k] = dvec[k] - c * uvp[k] - sl * A.inv_sigma;
         }
         __syncthreads();
         zmatvec(vr, vv);
