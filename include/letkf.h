@@ -33,7 +33,7 @@
  *     context's precision is LETKF_PREC_FP64, float otherwise.  Matrices are
  *     row-major with no padding: an (r x m) buffer holds element (i, j) at i*m + j.
  *   - Work is asynchronous.  Errors detected on the device (non-finite input,
- *     a bounded wait that ran out, an eigensolver that did not converge) are
+ *     a bounded wait that ran out, an iteration that hit its limit) are
  *     latched in the context and reported by letkf_sync (and by the next
  *     letkf_sync only: reading clears them).
  *   - A context is not thread-safe; distinct contexts are independent.
@@ -57,7 +57,9 @@ typedef enum letkf_status {
     LETKF_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
     LETKF_ENONFINITE = -5,  /* non-finite slopes: that frame was rejected, state unchanged */
     LETKF_ESTATE = -6,      /* call out of order (e.g. analyze twice without a forecast) */
-    LETKF_ENOCONV = -7,     /* a domain eigensolve hit its sweep limit (result still written) */
+    LETKF_ENOCONV = -7,     /* a domain's eigensolve (plain path: Jacobi sweeps) or inverse square
+                               root (fused and global paths: Newton-Schulz steps) hit its iteration
+                               limit (result still written) */
     LETKF_ESCRATCH = -8,    /* the problem does not fit letkf_analyze_static's fixed scratch */
     LETKF_EBUSY = -9        /* refused for now (letkf_serve.h): HBM budget or frame queue full */
 } letkf_status;
@@ -65,8 +67,10 @@ typedef enum letkf_status {
 typedef enum letkf_precision {
     LETKF_PREC_FP64 = 0,    /* everything in FP64 (plain path only) */
     LETKF_PREC_FP32 = 1,    /* everything in FP32 */
-    LETKF_PREC_MIXED = 2    /* BF16 tensor-core products with FP32 accumulation, FP32 eigensolve,
-                               FP64 eigenvalue functions and mean-weight sums (fused path only) */
+    LETKF_PREC_MIXED = 2    /* fused path only: BF16 tensor-core products with FP32 accumulation
+                               (single-BF16 Gram, split-BF16 Newton-Schulz and transform), mean
+                               weights refined in FP32 against the exact slopes, mean updates
+                               summed in FP64; small domains (simt_q_max) in FP32 on the CUDA cores */
 } letkf_precision;
 
 typedef enum letkf_path {
