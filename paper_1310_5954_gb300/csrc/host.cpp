@@ -720,7 +720,7 @@ const char* letkf_status_string(int s) {
         case LETKF_ETIMEOUT: return "a bounded device-side wait gave up";
         case LETKF_ENONFINITE: return "non-finite slopes: frame rejected, state unchanged";
         case LETKF_ESTATE: return "call out of order";
-        case LETKF_ENOCONV: return "an eigensolve reached its sweep limit";
+        case LETKF_ENOCONV: return "an eigensolve or inverse square root reached its iteration limit";
         case LETKF_ESCRATCH: return "problem too large for the fixed 16 MiB scratch of letkf_analyze_static";
         case LETKF_EBUSY: return "refused for now: HBM budget, pending-frame queue or batch slots full";
         default: return "unknown status";
