@@ -694,6 +694,11 @@ def main():
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "p50_ms": float(np.percentile(e2e_lat, 50)), "p99_ms": float(np.percentile(e2e_lat, 99))},
         "residual_rms": {"frames": W + K, "burn_in": burn, args.path: residual_rms(preds, phi, burn)},
+        # the paper's only timing (Sect. 4), on other hardware and another workload: context only
+        "paper_context": {"one_domain_update_s": 0.005, "loop_budget_s": 0.002,
+                          "hardware": "Intel Xeon W3565, 4 cores (CPU, precision not stated)",
+                          "workload": "40 m telescope, 69 domains, m = 197, n_max = 162, p_max = 242",
+                          "this_run_frame_s": 1e-3 * tot / K},
     }
     f.close()
     if world == 1 and not args.no_compare:
