@@ -698,7 +698,7 @@ def main():
         "paper_context": {"one_domain_update_s": 0.005, "loop_budget_s": 0.002,
                           "hardware": "Intel Xeon W3565, 4 cores (CPU, precision not stated)",
                           "workload": "40 m telescope, 69 domains, m = 197, n_max = 162, p_max = 242",
-                          "this_run_frame_s": 1e-3 * tot / K},
+                          "this_run_frame_s": tot / K},
     }
     f.close()
     if world == 1 and not args.no_compare:
