@@ -16,7 +16,9 @@ open-loop run; the loop adds the mirror and the metric, both here:
   the prediction x_hat(k+1|k), its piston removed over the pupil pixels; the coherent energy of
   the frame is the Marechal approximation exp(-variance), averaged over frames.
 
-Host-side numpy: this evaluates a control law, it is not part of the per-frame update.
+Host-side numpy and scipy.sparse (the influence functions are stored sparse: ~2.2 M entries for
+the 16 m system's 82 k pupil pixels): this evaluates a control law, it is not part of the per-frame
+update.
 """
 
 from __future__ import annotations
