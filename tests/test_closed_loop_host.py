@@ -92,3 +92,22 @@ def test_layers_add_up_to_the_total_r0():
               for s, (_, v, a) in zip(ts.screens, w.layers))
     np.testing.assert_allclose(phi1, ref, rtol=1e-12, atol=1e-12)
     assert not np.allclose(phi0, phi1)
+
+
+def test_pseudo_open_loop_slopes_equal_the_open_loop_ones():
+    # Sect. 3 closed loop: the sensor sees the residual phi - (mirror surface); adding back the
+    # sensor's response to the known mirror shape (its interaction with the commands) restores the
+    # open-loop slopes exactly, because the sensor is linear: the filter's input does not change
+    from synth import FineGridSensor
+    g, dm = _mirror(n_sub=8, obstruction=0.0, q=4)
+    sensor = FineGridSensor(8, 4)
+    rng = np.random.default_rng(5)
+    phi = rng.standard_normal(dm.pupil.shape)
+    x = rng.standard_normal(g.n_act)
+    surface = np.zeros(dm.pupil.shape)
+    surface[dm.pupil] = dm.correction(x)
+    ol = sensor.measure(phi)[:2]
+    cl = sensor.measure(phi - surface)[:2]
+    response = sensor.measure(surface)[:2]           # the interaction of the commands
+    for a, b, c in zip(ol, cl, response):
+        np.testing.assert_allclose((b + c)[g.sub_valid], a[g.sub_valid], rtol=0, atol=1e-12)
