@@ -266,3 +266,25 @@ def test_local_beats_global_at_equal_ensemble_size():
     local, glob = rms(doms), rms(None)
     phase = float(np.sqrt(np.mean((phi - phi.mean(axis=1, keepdims=True))[burn:] ** 2)))
     assert local < phase and glob > 10 * local
+
+
+def test_initial_ensemble_is_a_stationary_ar1_pair():
+    # second instant = L_stat xi0, first instant = a * second + L xi1, with xi from the seeded
+    # Philox streams (stream 0, counters 0 and 1); the second instant's sample covariance tends to
+    # L_stat L_stat^T
+    from oracle import philox
+    g = geometry.make_geometry(4, 0.0)
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((g.n_act, g.n_act))
+    L_stat = np.linalg.cholesky(B @ B.T / g.n_act + np.eye(g.n_act))
+    L = 0.1 * np.tril(rng.standard_normal((g.n_act, g.n_act)))
+    m, a, seed = 4000, 0.9, 17
+    f = etkf.OracleFilter(g, None, m, a, 0.1, seed=seed, L=L, L_stat=L_stat)
+    X = f.initial_ensemble()
+    xi0 = philox.normals(seed, 0, 0, m, g.n_act)
+    xi1 = philox.normals(seed, 0, 1, m, g.n_act)
+    np.testing.assert_allclose(X[g.n_act:], L_stat @ xi0, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(X[:g.n_act], a * (L_stat @ xi0) + L @ xi1, rtol=1e-13, atol=1e-13)
+    C = np.cov(X[g.n_act:])
+    S = L_stat @ L_stat.T
+    assert np.abs(C - S).max() < 6 * np.sqrt(2.0 / m) * np.abs(S).max()

@@ -99,3 +99,16 @@ def test_fried_matches_fine_sensor_at_one_sample_per_pitch():
     assert np.allclose(s[: g.n_subv], sx[g.sub_valid], atol=1e-12)
     assert np.allclose(s[g.n_subv:], sy[g.sub_valid], atol=1e-12)
     assert np.array_equal(pa, phi)
+
+
+def test_actuator_mask_brute_force():
+    # an actuator (grid corner) is valid iff at least one of the (up to four) subapertures it
+    # touches is valid
+    rng = np.random.default_rng(7)
+    for n in (1, 3, 6):
+        sub = rng.random((n, n)) < 0.5
+        act = geometry.actuator_mask(sub)
+        for i in range(n + 1):
+            for j in range(n + 1):
+                near = [sub[r, c] for r in (i - 1, i) for c in (j - 1, j) if 0 <= r < n and 0 <= c < n]
+                assert act[i, j] == any(near), (n, i, j)
