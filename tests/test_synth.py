@@ -101,3 +101,29 @@ def test_yule_walker_recovers_a_known_ar2_process():
     g = geometry.make_geometry(w.n_sub, w.obstruction)
     f1, f2 = w.ar2_fit(g.act_rc)
     assert abs(f2) < 1 and f1 + f2 < 1 and f2 - f1 < 1
+
+
+def test_lag_table_entries_are_the_covariance_at_the_shifted_lag():
+    from synth import actuator_covariance_lag_table, vk_phase_covariance
+    n, pitch, r0, L0, shift = 5, 0.5, 0.3, 25.0, (0.07, -0.02)
+    T = actuator_covariance_lag_table(n, pitch, r0, L0, shift)
+    assert T.shape == (2 * n - 1, 2 * n - 1)
+    for dr in range(-(n - 1), n):
+        for dc in range(-(n - 1), n):
+            r = np.hypot(pitch * dc + shift[0], pitch * dr + shift[1])
+            assert math.isclose(T[dr + n - 1, dc + n - 1], float(vk_phase_covariance(np.array(r), r0, L0)), rel_tol=1e-12)
+
+
+def test_nonstationary_schedule():
+    # the non-stationary ELT run: r0 halves at frame 3000 (phase std x 2^(5/6)), the wind goes
+    # linearly from 10 m/s along x to 25 m/s along y over frames 6000-7000, the slope noise steps
+    # from 0.1 to 0.3 rad at frame 8000; stationary workloads ignore the schedule
+    w = workload("elt-80x80-nonstationary")
+    assert w.screen_scale(2999) == 1.0 and math.isclose(w.screen_scale(3000), 2.0 ** (5.0 / 6.0))
+    assert w.wind_at(5999) == (10.0, 0.0) and w.wind_at(7000) == (25.0, math.pi / 2)
+    v, ang = w.wind_at(6500)
+    assert math.isclose(v, 17.5) and math.isclose(ang, math.pi / 4)
+    assert w.sigma_at(7999) == 0.1 and w.sigma_at(8000) == 0.3
+    s = workload("elt-80x80")
+    assert s.screen_scale(5000) == 1.0 and s.wind_at(6500) == (s.wind, s.wind_angle) and s.sigma_at(9000) == s.sigma
+    assert s.layer_list() == ((1.0, s.wind, s.wind_angle),)
