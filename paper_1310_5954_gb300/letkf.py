@@ -26,7 +26,12 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
                 q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0, p0_sqrt: Optional[np.ndarray] = None,
                 precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1,
                 ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0):
-    """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used)."""
+    """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used).
+
+    piston: "off", "output" or "in_loop" (differential-piston removal between domains);
+    simt_q_max: fused path, domains with min(p_loc, m) <= this take the FP32 analysis on the CUDA
+    cores (0: the library default, negative: every domain on the tensor cores).
+    """
     p = _lib.letkf_params()
     keep = []
     p.n_sub = int(n_sub)
