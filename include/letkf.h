@@ -175,6 +175,16 @@ int letkf_create(const letkf_params* params, letkf_ctx** out);
 int letkf_footprint(const letkf_params* params, unsigned long long* bytes);
 
 /*
+ * letkf_fused_plan: the fused path's launch plan for these parameters, computed on the host
+ * without a device (the same computation letkf_create makes): the dynamic shared memory of the
+ * fused kernel, the SIMT threshold in use (simt_q_max lowered until its workspace fits, 0 in the
+ * dual form m >= 128) and how many observing domains take the SIMT analysis.  LETKF_EINVAL for
+ * invalid parameters, a path other than LETKF_PATH_FUSED, or a system the fused kernel does not
+ * hold (more than 128 slopes per domain).  Outputs are host ints owned by the caller.
+ */
+int letkf_fused_plan(const letkf_params* params, int* smem_bytes, int* simt_q, int* n_domains_simt);
+
+/*
  * letkf_domain_tables: the geometry and domain decomposition letkf_create would build for these
  * parameters (Sect. 2.3; host only, no GPU).  sizes is filled first; every array may be NULL and
  * otherwise holds: own_off[n_dom + 1] / own[own_total] the valid actuators each domain updates

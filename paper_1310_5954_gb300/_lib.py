@@ -122,6 +122,8 @@ _SIGS = {
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_set_domain_mask": (ctypes.c_int, [_VP, _VP]),
     "letkf_global_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "letkf_fused_plan": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "letkf_piston_operator": (ctypes.c_int, [ctypes.POINTER(letkf_params), _VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
     "letkf_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(letkf_tuning)]),
@@ -296,6 +298,14 @@ def letkf_domain_tables(params: letkf_params) -> dict:
            "letkf_domain_tables")
     out.update({f: getattr(sz, f) for f, _ in letkf_domain_sizes._fields_})
     return out
+
+
+def letkf_fused_plan(params: letkf_params):
+    """(dynamic shared memory bytes, SIMT threshold, SIMT domains) of the fused path, host only."""
+    smem, q, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().letkf_fused_plan(ctypes.byref(params), ctypes.byref(smem), ctypes.byref(q), ctypes.byref(n)),
+           "letkf_fused_plan")
+    return smem.value, q.value, n.value
 
 
 def letkf_piston_operator(params: letkf_params):

@@ -1928,7 +1928,7 @@ FusedLayout fused_layout(const letkf_ctx* c) {
 
 }  // namespace
 
-int fused_prepare(letkf_ctx* c) {
+int fused_plan(letkf_ctx* c) {
     const HostModel& h = c->host;
     // the largest threshold (at most the one asked for) whose SIMT workspace fits shared memory
     c->simt_q = c->simt_ws = 0;
@@ -1955,6 +1955,13 @@ int fused_prepare(letkf_ctx* c) {
     if (L.total > 227 * 1024) return LETKF_EINVAL;
     if (h.n_h_max > 255 || h.n_loc_max > MT) return LETKF_EINVAL;
     c->fused_smem = L.total;
+    return LETKF_OK;
+}
+
+int fused_prepare(letkf_ctx* c) {
+    const HostModel& h = c->host;
+    const int rc = fused_plan(c);
+    if (rc) return rc;
     if (c->dual) {
         c->scratch_stride = std::max(h.n_h_max, 1) * c->m_pad;
         const size_t sb = (size_t)c->sms * c->scratch_stride * 4;

@@ -449,6 +449,34 @@ int letkf_footprint(const letkf_params* p, unsigned long long* bytes) {
     return LETKF_OK;
 }
 
+int letkf_fused_plan(const letkf_params* p, int* smem_bytes, int* simt_q, int* n_domains_simt) {
+    if (!p || !smem_bytes || !simt_q || !n_domains_simt) return LETKF_EINVAL;
+    *smem_bytes = *simt_q = *n_domains_simt = 0;
+    if (validate(p) || p->path != LETKF_PATH_FUSED) return LETKF_EINVAL;
+    letkf_ctx* c = new (std::nothrow) letkf_ctx();   // host fields only: no device state is made
+    if (!c) return LETKF_ENOMEM;
+    build_for(c->host, p);
+    const HostModel& h = c->host;
+    int rc = LETKF_EINVAL;
+    if (h.n_act > 0 && h.own_off.size() >= 2 && tables_in_bounds(h)) {
+        c->m = p->m;
+        c->m_pad = ((p->m + 3) / 4) * 4;             // the fused path's state is FP32
+        c->simt_q_max = p->simt_q_max;
+        c->n_dom = (int)h.own_off.size() - 1;
+        rc = letkf::fused_plan(c);
+        if (rc == LETKF_OK) {
+            *smem_bytes = c->fused_smem;
+            *simt_q = c->simt_q;
+            for (int d = 0; d < c->n_dom; ++d) {
+                const int no = h.obs_off[d + 1] - h.obs_off[d];
+                if (no > 0 && std::min(2 * no, c->m) <= c->simt_q) *n_domains_simt += 1;
+            }
+        }
+    }
+    delete c;
+    return rc;
+}
+
 int letkf_set_domain_mask(letkf_ctx* c, const unsigned char* active) {
     if (!c) return LETKF_EINVAL;
     if (c->path == LETKF_PATH_GLOBAL) return LETKF_EINVAL;

@@ -249,6 +249,9 @@ int noise_normals_params(letkf_ctx* c, unsigned long long frame, void* xi, Norma
 int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
 
 // fused.cu
+// Host only: the fused kernel's shared-memory plan (c->fused_smem, c->dual) and SIMT threshold
+// (c->simt_q, c->simt_ws) from the geometry, m, m_pad and simt_q_max; LETKF_EINVAL if it does not fit.
+int fused_plan(letkf_ctx* c);
 int fused_prepare(letkf_ctx* c);
 int fused_step(letkf_ctx* c, const void* y, double sigma, void* xpred, int with_forecast);
 // One launch of the fused kernel over the next frame of n systems (fused path, same device):

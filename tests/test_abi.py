@@ -115,3 +115,44 @@ def test_server_rejects_invalid_parameters(lib):
         assert lib.letkf_server_create(ctypes.byref(p), ctypes.byref(out)) == _lib.LETKF_EINVAL
         assert out.value is None
     assert lib.letkf_server_destroy(None) == _lib.LETKF_OK
+
+
+def _plan(**kw):
+    from paper_1310_5954_gb300.letkf import make_params
+    p, keep = make_params(path="fused", precision="mixed", ar1_a=0.99, sigma=0.1, **kw)
+    return _lib.letkf_fused_plan(p)
+
+
+ELT = dict(n_sub=80, obstruction=0.28, m=100, dom_sub=4, halo=2)
+
+
+@pytest.mark.parametrize("kw,q,n", [
+    (dict(n_sub=8, m=20, dom_sub=4, halo=1), 32, 4),       # every domain of a 20-member system
+    (ELT, 32, 16),                                          # the 16 edge domains with p_loc <= 24
+    (dict(ELT, simt_q_max=-1), 0, 0),                       # off
+    (dict(ELT, simt_q_max=24), 24, 16),
+    (dict(ELT, simt_q_max=64), 64, 40),
+    (dict(n_sub=40, obstruction=0.14, m=50, dom_sub=4, halo=2, simt_q_max=64), 64, 92),
+    (dict(ELT, m=150), 0, 0),                               # the dual form stays on the tensor cores
+])
+def test_fused_plan_simt_threshold(lib, kw, q, n):
+    smem, simt_q, n_simt = _plan(**kw)
+    assert (simt_q, n_simt) == (q, n)
+    assert 0 < smem <= 227 * 1024
+
+
+def test_fused_plan_lowers_the_threshold_to_fit_shared_memory(lib):
+    # every ELT domain would be q <= 100: the five q x q FP32 iteration matrices alone exceed what
+    # is left of 227 KB, so the threshold drops until the workspace fits
+    smem, q, n = _plan(**dict(ELT, simt_q_max=128))
+    assert 64 <= q < 100 and n >= 40 and smem <= 227 * 1024
+
+
+def test_fused_plan_rejects_other_paths_and_null_outputs(lib):
+    from paper_1310_5954_gb300.letkf import make_params
+    p, keep = make_params(n_sub=8, m=20, ar1_a=0.99, sigma=0.1, dom_sub=4, halo=1, path="plain")
+    one = ctypes.c_int()
+    assert lib.letkf_fused_plan(ctypes.byref(p), ctypes.byref(one), ctypes.byref(one), ctypes.byref(one)) == _lib.LETKF_EINVAL
+    p.path = _lib.LETKF_PATH_FUSED
+    assert lib.letkf_fused_plan(ctypes.byref(p), None, ctypes.byref(one), ctypes.byref(one)) == _lib.LETKF_EINVAL
+    assert lib.letkf_fused_plan(None, ctypes.byref(one), ctypes.byref(one), ctypes.byref(one)) == _lib.LETKF_EINVAL
