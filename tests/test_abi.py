@@ -156,3 +156,18 @@ def test_fused_plan_rejects_other_paths_and_null_outputs(lib):
     p.path = _lib.LETKF_PATH_FUSED
     assert lib.letkf_fused_plan(ctypes.byref(p), None, ctypes.byref(one), ctypes.byref(one)) == _lib.LETKF_EINVAL
     assert lib.letkf_fused_plan(None, ctypes.byref(one), ctypes.byref(one), ctypes.byref(one)) == _lib.LETKF_EINVAL
+
+
+def test_headers_are_plain_c(tmp_path):
+    # the boundary is a C ABI: both headers compile as strict C99 (and as C++)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "h.c"
+    src.write_text('#include "letkf.h"\n#include "letkf_serve.h"\nint main(void) { letkf_params p = {0}; (void)p; return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-fsyntax-only", str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
