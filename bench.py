@@ -133,7 +133,12 @@ def workload_inputs(wname, n_frames, sub_valid, act_valid):
 
 
 def residual_rms(xpred, phi, burn):
-    """sqrt of the mean over frames >= burn of ||phi_true(k+1) - x_hat(k+1|k)||^2 / n_act, piston removed."""
+    """sqrt of the mean over frames >= burn of ||phi_true(k+1) - x_hat(k+1|k)||^2 / n_act, piston removed.
+
+    Frame k's prediction is scored by the truth of frame k + 1, so at most len(phi) - 1 predictions
+    can be scored; more is a caller error."""
+    if len(xpred) > len(phi) - 1:
+        raise ValueError(f"{len(xpred)} predictions but truth for only {len(phi) - 1} of them")
     e = phi[1:len(xpred) + 1] - xpred
     e = e - e.mean(axis=1, keepdims=True)
     e = e[burn:]
@@ -279,7 +284,10 @@ def roofline(f, prof, sms, sm_max_mhz):
 
 
 def cpu_baseline(wname, y, seconds, L, Ls, piston="off"):
-    """The FP64 oracle as it stands, on this host's cores, over the first frames of the workload."""
+    """The FP64 oracle as it stands, on this host's cores, over the first frames of the workload.
+
+    y holds one more frame than can be scored (the truth of frame k + 1 scores frame k), so the
+    oracle steps at most len(y) - 1 frames, whatever the time budget."""
     from oracle import etkf, geometry
     from synth import workload
     w = workload(wname)
@@ -288,7 +296,7 @@ def cpu_baseline(wname, y, seconds, L, Ls, piston="off"):
     o = etkf.OracleFilter(g, doms, w.m, w.ar1_a, w.sigma, seed=w.seed, L=L, L_stat=Ls, piston=piston)
     preds = []
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds and len(preds) < len(y):
+    while time.perf_counter() - t0 < seconds and len(preds) < len(y) - 1:
         preds.append(o.step(y[len(preds)]))
     dt = time.perf_counter() - t0
     return len(preds) / dt, np.array(preds), len(preds), dt
