@@ -112,3 +112,65 @@ def test_actuator_mask_brute_force():
             for j in range(n + 1):
                 near = [sub[r, c] for r in (i - 1, i) for c in (j - 1, j) if 0 <= r < n and 0 <= c < n]
                 assert act[i, j] == any(near), (n, i, j)
+
+
+# Domain statistics of the workloads' systems under the reading above (half-illumination rule,
+# 4 x 4 blocks, last actuator row/column folded), counted independently of this module when the
+# hot-path scope was fixed: (N, obstruction, halo) -> (valid subapertures, valid actuators,
+# domains, n_loc min/median/max, p_loc min/median/max, sum p_loc); n_loc counts both state
+# instants, p_loc both slope directions.
+DOMAIN_STATS = [
+    ((8, 0.0, 1), (52, 69, 4, (26, 34, 44), (44, 44, 44), 176)),
+    ((40, 0.14, 2), (1240, 1332, 92, (2, 32, 40), (16, 124, 128), 9472)),
+    ((80, 0.28, 2), (4632, 4836, 332, (2, 32, 40), (16, 128, 128), 36328)),
+    ((16, 0.0, 2), (208, 241, 16, (12, 32, 40), (48, 88, 128), 1408)),
+    ((32, 0.10, 2), (808, 876, 60, (6, 32, 40), (38, 120, 128), 6088)),
+    ((64, 0.20, 2), (3104, 3256, 222, (2, 32, 40), (14, 128, 128), 24188)),
+    ((100, 0.28, 2), (7244, 7500, 505, (2, 32, 40), (20, 128, 128), 57028)),
+]
+
+
+@pytest.mark.parametrize("key,want", DOMAIN_STATS)
+def test_domain_statistics_of_the_workload_systems(key, want):
+    n, obs, h = key
+    g = geometry.make_geometry(n, obs)
+    doms = geometry.make_domains(g, 4, h)
+    nl = [2 * d.owned_act.size for d in doms]
+    pl = [2 * d.obs_sub.size for d in doms]
+    got = (g.n_subv, g.n_act, len(doms), (min(nl), int(np.median(nl)), max(nl)),
+           (min(pl), int(np.median(pl)), max(pl)), sum(pl))
+    assert got == want
+
+
+@pytest.mark.parametrize("n,obs,b,h", [(8, 0.0, 4, 1), (8, 0.0, 4, 0), (13, 0.2, 4, 2), (40, 0.14, 4, 2),
+                                       (80, 0.28, 4, 2), (10, 0.0, 3, 1), (9, 0.3, 5, 3)])
+def test_domains_equal_brute_force_membership(n, obs, b, h):
+    """Every domain's owned actuators and observed subapertures equal a brute-force membership test
+    written per element (distance of the element's grid cell to the block, clipped to the grid),
+    so a dropped or extra halo row or column, at the grid edge or inside, fails."""
+    g = geometry.make_geometry(n, obs)
+    doms = geometry.make_domains(g, b, h)
+    nb = -(-n // b)
+    by_block = {(d.I, d.J): d for d in doms}
+    # owned actuators: an actuator (r, c) belongs to the block whose span of subaperture rows and
+    # columns contains it; the corner row/column n lies past the last block and belongs to it
+    want_owned = {}
+    for k, (r, c) in enumerate(g.act_rc):
+        I = nb - 1 if r >= b * (nb - 1) else r // b
+        J = nb - 1 if c >= b * (nb - 1) else c // b
+        want_owned.setdefault((I, J), set()).add(k)
+    assert set(by_block) == set(want_owned)          # no block without valid actuators is kept
+    for IJ, d in by_block.items():
+        assert set(d.owned_act.tolist()) == want_owned[IJ]
+        assert np.all(np.diff(d.owned_act) > 0)
+        # observed subapertures: valid, and the Chebyshev gap between the subaperture's cell and
+        # the block's cells is at most the halo in each direction
+        I, J = IJ
+        want = set()
+        for k, (r, c) in enumerate(g.sub_rc):
+            gap_r = max(b * I - r, r - (b * (I + 1) - 1), 0)
+            gap_c = max(b * J - c, c - (b * (J + 1) - 1), 0)
+            if gap_r <= h and gap_c <= h:
+                want.add(k)
+        assert set(d.obs_sub.tolist()) == want, (IJ, sorted(want ^ set(d.obs_sub.tolist())))
+        assert np.all(np.diff(d.obs_sub) > 0)
