@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--ns-frames", type=int, default=10000, help="frames of the non-stationary serving run")
     ap.add_argument("--no-piston", action="store_true", help="skip the differential-piston leg")
     ap.add_argument("--no-global", action="store_true", help="skip the global-ETKF (m = 1024) leg")
+    ap.add_argument("--no-pair", action="store_true", help="skip the two-partition leg")
     ap.add_argument("--global-steps", type=int, default=200, help="timed steps of the global-ETKF leg")
     ap.add_argument("--oracle-probe", type=float, default=0.0,
                     help="(internal) time the oracle alone for this many seconds and print frames/s")
@@ -329,6 +330,46 @@ def piston_leg(w, path, precision, L, Ls, y, phi, n_frames, flush, tuning, torch
         if mode == "in_loop":
             preds_in_loop = preds
     return out, preds_in_loop
+
+
+def pair_leg(w, precision, L, Ls, y, phi, K, W, flush, torch, single_rms, burn, oracle_seconds):
+    """Two local ETKFs run together with two domain partitions (Sect. 5): the second filter's block
+    grid shifted by half a block, its own seed; the output is the mean of the two predictions
+    (letkf_step_pair, both filters' domains in one fused launch).  Per-step time (CUDA events, L2
+    flushed before each step) and residual RMS on the headline frames next to the single filter's;
+    the FP64 oracle's pair (two oracle filters averaged) on the first frames, bounded in time."""
+    from paper_1310_5954_gb300 import LETKFPair
+    p = LETKFPair(n_sub=w.n_sub, m=w.m, ar1_a=w.ar1_a, sigma=w.sigma, dom_sub=w.dom_sub, halo=w.halo,
+                  obstruction=w.obstruction, q_sqrt=L, p0_sqrt=Ls, precision=precision, seed=w.seed,
+                  obs_block=w.obs_block)
+    ydev = torch.as_tensor(y, dtype=p.dtype, device=p.device).contiguous()
+    ms, preds, _ = run_device(p, ydev, K, W, flush, torch)
+    status = p.sync()
+    p.close()
+    out = {"workload": f"{w.name}: two filters, block grids offset by {w.dom_sub // 2} subapertures, seeds "
+                       f"{w.seed} and {w.seed + 1}, output the mean prediction",
+           "frames_per_s": K / (sum(ms) / 1e3), "p50_ms": float(np.percentile(ms, 50)),
+           "p99_ms": float(np.percentile(ms, 99)),
+           "residual_rms": {"frames": W + K, "burn_in": burn, "pair": residual_rms(preds, phi, burn),
+                            "single": single_rms},
+           "device_status": status}
+    if oracle_seconds > 0:
+        from oracle import etkf, geometry
+        g = geometry.make_geometry(w.n_sub, w.obstruction)
+        mk = lambda off, seed: etkf.OracleFilter(g, geometry.make_domains(g, w.dom_sub, w.halo, offset=off), w.m,
+                                                 w.ar1_a, w.sigma, seed=seed, L=L, L_stat=Ls, obs_block=w.obs_block)
+        oa, ob = mk(0, w.seed), mk(w.dom_sub // 2, w.seed + 1)
+        op = []
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < oracle_seconds and len(op) < len(y) - 1:
+            k = len(op)
+            op.append(0.5 * (oa.step(y[k]) + ob.step(y[k])))
+        nf = len(op)
+        nb = min(burn, max(nf - 2, 0))
+        out["oracle_first_frames"] = {"frames": nf, "burn_in": nb, "oracle_pair": residual_rms(np.array(op), phi, nb),
+                                      "gpu_pair": residual_rms(preds[:nf], phi, nb),
+                                      "seconds": time.perf_counter() - t0}
+    return out
 
 
 def global_leg(steps, warmup, flush, torch, workers=16):
@@ -724,6 +765,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_piston:
         out["piston_removal"], preds_pl = piston_leg(w, args.path, precision, L, Ls, y, phi, args.piston_frames,
                                                      flush, tuned.get(args.path, {}).get("tuning"), torch)
+    if rank == 0 and world == 1 and not args.no_pair and args.path == "fused":
+        out["two_partitions"] = pair_leg(w, precision, L, Ls, y, phi, K, W, flush, torch,
+                                         out["residual_rms"][args.path], burn,
+                                         0.0 if args.no_cpu_baseline else args.cpu_seconds / 2)
     if rank == 0 and world == 1 and not args.no_global:
         out["global_etkf"] = global_leg(args.global_steps, 5, flush, torch)
         out["global_etkf"]["same_m_as_local"] = etkf_vs_letkf(w, L, Ls, y, phi, burn,

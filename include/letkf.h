@@ -53,7 +53,7 @@ typedef enum letkf_status {
     LETKF_OK = 0,
     LETKF_EINVAL = -1,      /* invalid argument or unsupported configuration */
     LETKF_ENOMEM = -2,      /* device or host allocation failed */
-    LETKF_ECUDA = -3,       /* a CUDA runtime or cuBLAS call failed */
+    LETKF_ECUDA = -3,       /* a CUDA runtime call failed */
     LETKF_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
     LETKF_ENONFINITE = -5,  /* non-finite slopes: that frame was rejected, state unchanged */
     LETKF_ESTATE = -6,      /* call out of order (e.g. analyze twice without a forecast) */
@@ -135,6 +135,11 @@ typedef struct letkf_params {
                                        tensor-core products; 0 selects the default (32), a negative
                                        value turns it off, at most 128.  Lowered at create time to
                                        what shared memory holds. */
+    int dom_offset;                 /* shift of the block grid, in subapertures along both axes,
+                                       0 <= dom_offset < dom_sub: block (I, J) spans subaperture
+                                       rows [dom_sub I - dom_offset, dom_sub (I + 1) - dom_offset)
+                                       and columns likewise (the second partition of the two
+                                       parallel local filters of Sect. 5; letkf_step_pair) */
 } letkf_params;
 
 typedef struct letkf_info {
@@ -230,6 +235,23 @@ int letkf_gemm_selftest(const float* A, const float* B, float* C, int M, int N, 
 int letkf_global_stats(letkf_ctx* ctx, int* ns_steps, double* s_bound);
 
 /*
+ * letkf_set_capture (tests, LETKF_PATH_FUSED): from the next analysis on, the analysis of domain
+ * `domain` (numbering of letkf_domain_tables) also writes what it computed for the transform of
+ * Sect. 2.2-2.3 (w_bar = [(m-1)I + G]^-1 Y'^T R^-1 d and T = sqrt(m-1) [(m-1)I + G]^(-1/2)) into
+ * cap_dev, a caller-owned device array of cap_floats FP32 elements, at least
+ * 8 + m + max(m * m, 2 * p_loc_max * m).  Layout: [0] form (0: m x m form on the tensor cores,
+ * 1: observation-space form on the tensor cores, 2: m x m form on the CUDA cores, 3:
+ * observation-space form on the CUDA cores), [1] q (m for forms 0 and 2, the domain's slope
+ * count p for 1 and 3), [2] the conditioning bound s = 1 + ||G||_F/(m-1), [3] Newton-Schulz
+ * steps, [4..7] zero; then w_bar (m); then for forms 0 and 2 T (m x m, row-major), for forms 1
+ * and 3 W (q x m) and M = (I + Z)^-1 W (q x m), row-major, with T = I - W^T M.  A domain the
+ * frame skips (no observation, rejected frame) writes nothing.  cap_dev == NULL stops the
+ * capture.  LETKF_ESTATE on other paths, LETKF_EINVAL for a domain out of range or too small an
+ * array.  The array must stay allocated while captured frames run.
+ */
+int letkf_set_capture(letkf_ctx* ctx, int domain, float* cap_dev, long long cap_floats);
+
+/*
  * letkf_set_domain_mask (fault injection, local paths): active[d] == 0 skips domain d from the
  * next analysis on: its actuators keep their forecast, as a domain without observations does
  * (Sect. 2.3; a lost node of a distributed implementation).  active has n_dom entries in the
@@ -274,6 +296,19 @@ int letkf_forecast(letkf_ctx* ctx, const void* v_dev);
  */
 int letkf_step(letkf_ctx* ctx, const void* y_dev, double sigma, void* xpred_dev);
 
+/*
+ * letkf_step_pair: two local ETKFs run together on the same slopes, with two different domain
+ * partitions (Sect. 5), and their predictions combined: one letkf_step of each filter, both
+ * filters' domains analysed in one launch of the fused kernel, then xpred_dev (n_act elements,
+ * FP32, required) = (x_hat_a + x_hat_b) / 2.  Each filter keeps its own ensemble, noise draws and
+ * frame counter; neither sees the other's estimate (the combination is the output only).  The
+ * partitions differ by letkf_params.dom_offset (e.g. 0 and dom_sub / 2), the noise streams by
+ * the seed.  Requirements (else LETKF_EINVAL): two distinct fused-path contexts on the same
+ * device and the same stream, the same pupil (n_act and p), differential pistons off; both in
+ * the forecast phase (else LETKF_ESTATE).  A frame with a non-finite slope is rejected by both.
+ */
+int letkf_step_pair(letkf_ctx* a, letkf_ctx* b, const void* y_dev, double sigma, void* xpred_dev);
+
 /* Ensemble as an n x m matrix (state type) and the frame counter (either may be NULL). */
 int letkf_get_state(letkf_ctx* ctx, void* x_dev, unsigned long long* frame);
 
@@ -317,7 +352,7 @@ int letkf_autotune(letkf_ctx* ctx, const void* y_dev, int frames, letkf_tuning* 
 int letkf_sync(letkf_ctx* ctx);
 
 /*
- * letkf_analyze_static: the analysis of letkf_analyze (plain path, Sect. 2.3) without any
+ * letkf_analyze_static: the analysis of letkf_analyze on a plain-path context, without any
  * allocation, for callers that cannot call the CUDA allocator while they run, e.g. a real-time
  * controller that reserves its device memory before its loop and must not block on or fail in
  * an allocation with a frame deadline pending.  The paper has no counterpart.
@@ -334,8 +369,9 @@ int letkf_sync(letkf_ctx* ctx);
  * ~43 MiB; the 8x8 and 40x40 systems fit).  Every call shares that array and it keeps the last
  * call's contents: calls whose work may overlap on the device (other streams, other contexts
  * on the same GPU) race and must be serialised by the caller.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Plain-path contexts only (LETKF_EINVAL otherwise); requires the forecast phase
+ * up the array's device address (cudaGetSymbolAddress) and raises the analysis kernels'
+ * dynamic shared-memory limit (as letkf_analyze's first call does); make that first call before
+ * any stream capture.  Plain-path contexts only (LETKF_EINVAL otherwise); requires the forecast phase
  * (LETKF_ESTATE).
  */
 int letkf_analyze_static(letkf_ctx* ctx, const void* y_dev, double sigma, void* xa_dev);

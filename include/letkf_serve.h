@@ -54,6 +54,10 @@ typedef struct letkf_frame_record {
     long long t_done_ns;            /* completion seen by the host (prediction in host memory) */
     int batch_systems;              /* systems in that batch */
     int slot;                       /* stream slot of that batch */
+    long long t_dev_start_ns;       /* device clock (CUDA events, from the server's creation): the
+                                       batch's first operation on its slot's stream (slope copy) */
+    long long t_dev_end_ns;         /* and its last (prediction copied out); batches in different
+                                       slots whose intervals intersect ran on the device together */
 } letkf_frame_record;
 
 typedef struct letkf_server_info {

@@ -118,28 +118,35 @@ class Domain:
         return np.concatenate([self.obs_sub, self.obs_sub + n_subv])
 
 
-def make_domains(geom: Geometry, dom_sub: int, halo: int) -> List[Domain]:
-    """Domain decomposition of Sect. 2.3 under the reading in the module docstring."""
+def make_domains(geom: Geometry, dom_sub: int, halo: int, offset: int = 0) -> List[Domain]:
+    """Domain decomposition of Sect. 2.3 under the reading in the module docstring.
+
+    offset shifts the block grid by that many subapertures along both axes (block I spans
+    subaperture rows [b I - offset, b (I + 1) - offset)), giving the second partition of the
+    two-partition variant of Sect. 5; offset 0 is the partition described above."""
     n = geom.n_sub
     b = dom_sub
-    nb = -(-n // b)
+    if not 0 <= offset < b:
+        raise ValueError("offset must lie in [0, dom_sub)")
+    nb = -(-(n + offset) // b)
+    last = (n - 1 + offset) // b          # block of the last subaperture row; row n folds into it
     doms = []
     for I in range(nb):
         for J in range(nb):
             owned = []
             for r in range(n + 1):
-                if min(r // b, nb - 1) != I:
+                if min((r + offset) // b, last) != I:
                     continue
                 for c in range(n + 1):
-                    if min(c // b, nb - 1) != J:
+                    if min((c + offset) // b, last) != J:
                         continue
                     if geom.act_valid[r, c]:
                         owned.append(geom.act_index[r, c])
             if not owned:
                 continue
             obs = []
-            for r in range(max(0, b * I - halo), min(n, b * (I + 1) + halo)):
-                for c in range(max(0, b * J - halo), min(n, b * (J + 1) + halo)):
+            for r in range(max(0, b * I - offset - halo), min(n, b * (I + 1) - offset + halo)):
+                for c in range(max(0, b * J - offset - halo), min(n, b * (J + 1) - offset + halo)):
                     if geom.sub_valid[r, c]:
                         obs.append(geom.sub_index[r, c])
             doms.append(Domain(I, J, np.array(sorted(owned), dtype=np.int64),

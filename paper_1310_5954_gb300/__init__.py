@@ -10,5 +10,5 @@ PyTorch is used for device memory and streams only.
 
 from ._lib import (LETKF_PATH_FUSED, LETKF_PATH_PLAIN, LETKF_PREC_FP32, LETKF_PREC_FP64,  # noqa: F401
                    LETKF_PREC_MIXED, LETKFError, load)
-from .letkf import LETKF, footprint  # noqa: F401
+from .letkf import LETKF, LETKFPair, footprint  # noqa: F401
 from .serve import Server  # noqa: F401

@@ -44,6 +44,7 @@ class letkf_params(ctypes.Structure):
         ("ar2_a", ctypes.c_double),
         ("piston", ctypes.c_int),
         ("simt_q_max", ctypes.c_int),
+        ("dom_offset", ctypes.c_int),
     ]
 
 
@@ -67,7 +68,8 @@ class letkf_server_params(ctypes.Structure):
 class letkf_frame_record(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int), ("status", ctypes.c_int), ("frame", ctypes.c_ulonglong),
                 ("t_arrival_ns", ctypes.c_longlong), ("t_launch_ns", ctypes.c_longlong),
-                ("t_done_ns", ctypes.c_longlong), ("batch_systems", ctypes.c_int), ("slot", ctypes.c_int)]
+                ("t_done_ns", ctypes.c_longlong), ("batch_systems", ctypes.c_int), ("slot", ctypes.c_int),
+                ("t_dev_start_ns", ctypes.c_longlong), ("t_dev_end_ns", ctypes.c_longlong)]
 
 
 class letkf_server_info(ctypes.Structure):
@@ -122,6 +124,8 @@ _SIGS = {
     "letkf_get_graph": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "letkf_set_domain_mask": (ctypes.c_int, [_VP, _VP]),
     "letkf_global_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "letkf_set_capture": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong]),
+    "letkf_step_pair": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP]),
     "letkf_fused_plan": (ctypes.c_int, [ctypes.POINTER(letkf_params), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "letkf_piston_operator": (ctypes.c_int, [ctypes.POINTER(letkf_params), _VP, ctypes.POINTER(ctypes.c_int)]),
@@ -329,6 +333,14 @@ def letkf_global_stats(ctx: int):
     sb = ctypes.c_double()
     _check(load().letkf_global_stats(ctx, ctypes.byref(n), ctypes.byref(sb)), "letkf_global_stats")
     return n.value, sb.value
+
+
+def letkf_step_pair(ctx_a: int, ctx_b: int, y_ptr: int, sigma: float, xpred_ptr: int) -> int:
+    return _check(load().letkf_step_pair(ctx_a, ctx_b, y_ptr, sigma, xpred_ptr), "letkf_step_pair")
+
+
+def letkf_set_capture(ctx: int, domain: int, cap_ptr: int, cap_floats: int) -> int:
+    return _check(load().letkf_set_capture(ctx, domain, cap_ptr, cap_floats), "letkf_set_capture")
 
 
 def letkf_footprint(params: letkf_params) -> int:

@@ -1,7 +1,8 @@
 """Build libletkf.so in-tree with nvcc for sm_103a (GB300).
 
-Each translation unit is compiled in parallel, then linked with cuBLAS.  The
-library is written next to this file (lib/libletkf.so) and is git-ignored.
+Each translation unit is compiled in parallel, then linked against the CUDA runtime
+only (every kernel is the library's own).  The library is written next to this file
+(lib/libletkf.so) and is git-ignored.
 """
 
 from __future__ import annotations
@@ -58,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         futs = [ex.submit(_compile, nvcc, s, o, verbose) for s, o in zip(SOURCES, objs)]
         for f in futs:
             f.result()
-    cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcublas", "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -41,8 +41,9 @@ constexpr int FT = 256;                  // threads per CTA
 constexpr int MT = 128;                  // MMA rows
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: a wait that long means a fault
 // ||I - P||_F below which the next Newton-Schulz update is the last: the update squares it
-// (~0.75 ||I - P||^2), under the split-BF16 rounding of the iteration for FP32 results, and under
-// the single-BF16 rounding of the Gram and transform (~2^-9) for mixed-precision ones.
+// (~0.75 ||I - P||^2), under the split-BF16 rounding of the iteration when the Gram is accurate to
+// FP32, and under the rounding of a Gram formed from single-BF16 operands (~2^-9, mixed precision
+// with the conditioning bound s <= s_split).
 constexpr float NS_LAST_FP32 = 2e-2f, NS_LAST_MIXED = 1.2e-1f;
 // Newton-Schulz runs on A_s = (I + G/c)/s_ns with s_ns = s/NS_SCALE, s = 1 + ||G||_F/c: the
 // eigenvalues of A_s stay below NS_SCALE = 2.5 (||G||_F bounds the largest eigenvalue of G), inside
@@ -77,7 +78,8 @@ struct SysDesc {
     int m, m_pad, n_act, n_subv, n_dom, row_obs, NP, KP, RA, item0;
     float inv_sigma, a, q_white;
     float a2;            // AR coefficient of the second instant (0: AR(1))
-    float ns_last;       // ||I - P||_F below which the next Newton-Schulz update is the last
+    float ns_last;       // ||I - P||_F below which the next Newton-Schulz update is the last, when the
+                         // Gram was rounded to single BF16 (else NS_LAST_FP32: see ns_stop)
     int simt_q;          // domains with min(p_loc, m) <= simt_q take the FP32 SIMT analysis (0: none)
     int vmode, with_forecast, gram_terms, tr_terms, max_it;
     float s_split;       // mixed precision: conditioning bound above which the Gram is split
@@ -85,7 +87,30 @@ struct SysDesc {
     // shared-memory layout (bytes from the dynamic base); vec and XE start at the same offset
     // for every system, so a region below off_big never overlaps another system's operands
     int off_vec, off_xe, off_xh, off_big, sz_op, sz_opg, sz_a;
+    // test instrument: when cap is set, the analysis of domain cap_dom writes what it computed
+    // (header, mean weights, transform or its factors; layout in letkf_set_capture) to cap
+    float* cap;
+    int cap_dom;
 };
+
+// Header of a capture: the form of the analysis, the dimension of the iteration, the conditioning
+// bound s and the Newton-Schulz steps taken.
+constexpr int CAP_HDR = 8;
+enum { CAP_MM_TENSOR = 0, CAP_DUAL_TENSOR = 1, CAP_MM_SIMT = 2, CAP_DUAL_SIMT = 3 };
+// The stop threshold of the Newton-Schulz iteration follows the rounding of the Gram it inverts:
+// the precision's threshold when the Gram's operands were single BF16 (mixed precision, bound s
+// <= s_split), the FP32 one when they were split or the Gram was formed in FP32 (SIMT analysis).
+__device__ __forceinline__ float ns_stop(float ns_last, int gram_terms, float s_scale, float s_split) {
+    return (gram_terms < 3 && s_scale <= s_split) ? ns_last : NS_LAST_FP32;
+}
+
+__device__ __forceinline__ void cap_header(float* cap, int form, int q, float s, int it) {
+    cap[0] = (float)form;
+    cap[1] = (float)q;
+    cap[2] = s;
+    cap[3] = (float)it;
+    for (int t = 4; t < CAP_HDR; ++t) cap[t] = 0.f;
+}
 
 struct Ctrl {
     uint64_t bar_load;
@@ -456,6 +481,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const float s_scale = 1.f + sqrtf(fro) / c;
     const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
     const float inv_cs = 1.f / (c * s_ns);
+    const float ns_last = ns_stop(A.ns_last, A.gram_terms, s_scale, A.s_split);
     // ---- Z = ((I + K/c)/s)^(-1/2) by the coupled Newton-Schulz iteration (dimension P)
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {
@@ -526,7 +552,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
         z_in_tmem = true;
         to_mma();
-        if (rn < A.ns_last) break;     // as in the m x m form: the last update lands at the floor
+        if (rn < ns_last) break;       // as in the m x m form: the last update lands at the floor
     }
     if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
     tc_fence_before();
@@ -614,6 +640,11 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         __syncthreads();
     }
     st_times(uvp, wbar);
+    const bool cap = A.cap != nullptr && d == A.cap_dom;
+    if (cap) {
+        if (tid == 0) cap_header(A.cap, CAP_DUAL_TENSOR, P, s_scale, it);
+        for (int t = tid; t < m; t += FT) A.cap[CAP_HDR + t] = wbar[t];
+    }
     // ---- (I + Z)^-1, Z = Z_ns / sqrt(s), by Newton's iteration X <- X (2I - (I + Z) X) from
     //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G
     const float rs = rsqrtf(s_ns);
@@ -728,6 +759,10 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
 #pragma unroll
         for (int u = 0; u < 8; ++u) wv[u] = (row < P && mcol0 + 8 * q8 + u < m) ? wv[u] : 0.f;
         if (row < NP) store8(Wh, Wl, row, mcol0 + 8 * q8, MP, wv, true);
+        if (cap && row < P)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (mcol0 + 8 * q8 + u < m) A.cap[CAP_HDR + m + row * m + mcol0 + 8 * q8 + u] = wv[u];
     }
     unsigned char* A1h = big;                       // X'_E (RA x MP) over Z's operand
     unsigned char* A1l = big + RA * MP * 2;
@@ -789,6 +824,10 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
 #pragma unroll
         for (int u = 0; u < 8; ++u) wv[u] = (row < P && mcol0 + 8 * q8 + u < m) ? wv[u] : 0.f;
         if (row < NP) store8(Wh, Wl, row, mcol0 + 8 * q8, MP, wv, true);
+        if (cap && row < P)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (mcol0 + 8 * q8 + u < m) A.cap[CAP_HDR + m + (P + row) * m + mcol0 + 8 * q8 + u] = wv[u];
     }
     to_mma();
     if (tid == 0) {
@@ -1101,7 +1140,7 @@ __device__ __noinline__ const float* analyse_simt(const FusedBatch& B, Ctrl* ctl
             simt_mm(Zn, lq, T, lq, 1, Z, lq, 1, q, q, q, 1.f);       // T Z
             float* sy = Y; Y = Yn; Yn = sy;
             float* sz = Z; Z = Zn; Zn = sz;
-            if (rn < A.ns_last) break;
+            if (rn < NS_LAST_FP32) break;      // the Gram here is FP32 (see ns_stop)
         }
     if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
     // ---- mean weights, refined against the exact operator
@@ -1138,6 +1177,11 @@ __device__ __noinline__ const float* analyse_simt(const FusedBatch& B, Ctrl* ctl
             __syncthreads();
         }
     }
+    const bool cap = A.cap != nullptr && d == A.cap_dom;
+    if (cap) {
+        if (tid == 0) cap_header(A.cap, dual ? CAP_DUAL_SIMT : CAP_MM_SIMT, q, s_scale, it);
+        for (int t = tid; t < m; t += FT) A.cap[CAP_HDR + t] = wbar[t];
+    }
     // ---- own rows: means, mean update, centred anomalies X'_E; then the next item's loads
     own_row_means(A, XE, n_e, wbar, xe_mean, uvec);
     for (int t = tid; t < n_e * m; t += FT) {
@@ -1150,6 +1194,8 @@ __device__ __noinline__ const float* analyse_simt(const FusedBatch& B, Ctrl* ctl
     const float rs = rsqrtf(s_ns);    // T = Z / sqrt(s_ns) (m x m form); Z / sqrt(s_ns) = (I + K/c)^(-1/2)
     *ld_out = lm;
     if (!dual) {
+        if (cap)
+            for (int t = tid; t < m * m; t += FT) A.cap[CAP_HDR + m + t] = rs * Z[(t / m) * lq + t % m];
         simt_mm(Out, lm, E, lm, 1, Z, lq, 1, n_e, m, m, rs);
         return Out;
     }
@@ -1170,6 +1216,11 @@ __device__ __noinline__ const float* analyse_simt(const FusedBatch& B, Ctrl* ctl
         simt_mm(Q, lq, Mi, lq, 1, X, lq, 1, q, q, q, -1.f, 2.f);     // 2I - (I + Zt) X
         simt_mm(Xn, lq, X, lq, 1, Q, lq, 1, q, q, q, 1.f);
         float* sx = X; X = Xn; Xn = sx;
+    }
+    if (cap) {     // W = Zt S / sqrt(c) and (I + Zt)^-1 W, the factors of T = I - W^T (I + Zt)^-1 W
+        float* Wc = A.cap + CAP_HDR + m;
+        simt_mm(Wc, m, Z, lq, 1, S, lm, 1, q, m, q, rs * rsqrtf(c));
+        simt_mm(Wc + q * m, m, X, lq, 1, Wc, m, 1, q, m, q, 1.f);
     }
     simt_mm(R1, lq, E, lm, 1, S, 1, lm, n_e, q, m, 1.f);              // X'_E S^T
     simt_mm(R2, lq, R1, lq, 1, Z, lq, 1, n_e, q, q, rs);              // X'_E W^T sqrt(c)
@@ -1397,6 +1448,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             const float s_scale = 1.f + sqrtf(fro) / c;
             const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
             const float inv_cs = 1.f / (c * s_ns);
+            const float ns_last = ns_stop(A.ns_last, A.gram_terms, s_scale, A.s_split);
             // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
             //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
             //      Z_1 = T_0: one pass over G writes Y_0, T_0 (also as Z_1) and the residual.
@@ -1536,7 +1588,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 __syncthreads();
                 // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the rounding of
                 // the result once ||I - P|| < ns_last: the product that would confirm it is skipped
-                if (rn < A.ns_last) break;
+                if (rn < ns_last) break;
             }
             if (!ok) break;
             if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
@@ -1639,6 +1691,11 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 if (hh == 0 && row < m) wbar[row] += vv[row] * inv_cs;
                 __syncthreads();
             }
+            const bool cap = A.cap != nullptr && d == A.cap_dom;
+            if (cap) {
+                if (tid == 0) cap_header(A.cap, CAP_MM_TENSOR, m, s_scale, it);
+                for (int t = tid; t < m; t += FT) A.cap[CAP_HDR + t] = wbar[t];
+            }
             // ---- 5. transform: X_a[E] = x_bar 1^T + (X'_E w_bar) 1^T + centred(X'_E T).  In exact
             //        arithmetic T 1 = 1 and X'_E 1 = 0, so X'_E T has zero member mean and this is
             //        x_bar 1^T + X'_E (w_bar 1^T + T); centring the product keeps the analysis mean
@@ -1652,6 +1709,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 for (int u = 0; u < 8; ++u) {
                     const int j = col0 + 8 * q8 + u;
                     bv[u] = (row < m && j < m) ? zv[u] * rs : 0.f;
+                    if (cap && row < m && j < m) A.cap[CAP_HDR + m + row * m + j] = bv[u];
                 }
                 if (row < NP) store8(Bh, Bl, row, col0 + 8 * q8, NP, bv, A.tr_terms > 1);
             }
@@ -1978,8 +2036,6 @@ int fused_prepare(letkf_ctx* c) {
     int prio_least = 0, prio_greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) return LETKF_ECUDA;
     if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess) return LETKF_ECUDA;
-    if (cublasCreate(&c->cublas_side) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
-    if (cublasSetStream(c->cublas_side, c->side) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     const size_t vbytes = (size_t)c->n_act * c->m_pad * 4;
     const size_t xbytes = c->precision == LETKF_PREC_MIXED ? noise_xi_bytes(c->n_act, c->m)
                                                            : vbytes;
@@ -1989,14 +2045,14 @@ int fused_prepare(letkf_ctx* c) {
         if (cudaMalloc(&c->Vbuf[b], vbytes) != cudaSuccess) return LETKF_ENOMEM;
         c->device_bytes += vbytes;
     }
+    if (cudaMalloc(&c->pair_pred, (size_t)c->n_act * 4) != cudaSuccess) return LETKF_ENOMEM;
+    c->device_bytes += (size_t)c->n_act * 4;
     if (cudaMalloc(&c->Xi_side, xbytes) != cudaSuccess) return LETKF_ENOMEM;
     if (cudaMemset(c->Xi_side, 0, xbytes) != cudaSuccess) return LETKF_ECUDA;   // tile padding stays zero
     c->device_bytes += xbytes;
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cublasCreate(&c->cublas_cap) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetStream(c->cublas_cap, c->cap_stream) != CUBLAS_STATUS_SUCCESS)
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return LETKF_ECUDA;
     c->graph_on = 0;
     return LETKF_OK;
@@ -2010,7 +2066,7 @@ int noise_ready(letkf_ctx* c, unsigned long long frame, cudaStream_t stream, con
     const int b = (int)(frame & 1);
     if (c->v_frame[b] != frame) {
         if (cudaStreamWaitEvent(c->side, c->ev_v_used[b], 0) != cudaSuccess) return LETKF_ECUDA;
-        const int rc = draw_perturbations_on(c, frame, c->Xi_side, c->Vbuf[b], c->side, c->cublas_side);
+        const int rc = draw_perturbations_on(c, frame, c->Xi_side, c->Vbuf[b], c->side);
         if (rc) return rc;
         if (cudaEventRecord(c->ev_v_ready[b], c->side) != cudaSuccess) return LETKF_ECUDA;
         c->v_frame[b] = frame;
@@ -2027,7 +2083,7 @@ int noise_prefetch(letkf_ctx* c, unsigned long long frame, cudaStream_t stream) 
     if (cudaEventRecord(c->ev_v_used[b], stream) != cudaSuccess) return LETKF_ECUDA;
     if (c->v_frame[nb] == frame + 1) return LETKF_OK;
     if (cudaStreamWaitEvent(c->side, c->ev_v_used[nb], 0) != cudaSuccess) return LETKF_ECUDA;
-    const int rc = draw_perturbations_on(c, frame + 1, c->Xi_side, c->Vbuf[nb], c->side, c->cublas_side);
+    const int rc = draw_perturbations_on(c, frame + 1, c->Xi_side, c->Vbuf[nb], c->side);
     if (rc) return rc;
     if (cudaEventRecord(c->ev_v_ready[nb], c->side) != cudaSuccess) return LETKF_ECUDA;
     c->v_frame[nb] = frame + 1;
@@ -2089,6 +2145,8 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->sz_op = L.sz_op;
     S->sz_opg = L.sz_opg;
     S->sz_a = L.sz_a;
+    S->cap = c->cap_dev;
+    S->cap_dom = c->cap_dom;
 }
 
 // Descriptor of system c's next frame; `stream` (the kernel's) waits for its noise block.
@@ -2202,7 +2260,7 @@ int graph_capture(letkf_ctx* c, int p) {
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         ok = cudaLaunchKernelExC(&cfg, nn.params.func, nn.params.kernelParams) == cudaSuccess &&
-             draw_product_on(c, c->Xi_side, c->Vbuf[p ^ 1], cs, c->cublas_cap) == LETKF_OK;
+             draw_product_on(c, c->Xi_side, c->Vbuf[p ^ 1], cs) == LETKF_OK;
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
@@ -2331,6 +2389,64 @@ extern "C" int letkf_umma_selftest(const float* A, const float* B, float* D, int
     cudaFree(st);
     if (e != cudaSuccess || e2 != cudaSuccess) return LETKF_ECUDA;
     return h ? LETKF_ETIMEOUT : LETKF_OK;
+}
+
+namespace letkf {
+namespace {
+
+// x_hat of the two filters of letkf_step_pair, averaged: out = (a + b) / 2.
+__global__ void pair_mean_kernel(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out,
+                                 int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = 0.5f * (a[i] + b[i]);
+}
+
+}  // namespace
+}  // namespace letkf
+
+extern "C" int letkf_step_pair(letkf_ctx* a, letkf_ctx* b, const void* y_dev, double sigma, void* xpred_dev) {
+    using namespace letkf;
+    if (!a || !b || a == b || !y_dev || !xpred_dev) return LETKF_EINVAL;
+    if (a->path != LETKF_PATH_FUSED || b->path != LETKF_PATH_FUSED || a->device != b->device ||
+        a->stream != b->stream || a->n_act != b->n_act || a->p != b->p || a->piston != LETKF_PISTON_OFF ||
+        b->piston != LETKF_PISTON_OFF)
+        return LETKF_EINVAL;
+    if (a->phase != 0 || b->phase != 0) return LETKF_ESTATE;
+    if (cudaSetDevice(a->device) != cudaSuccess) return LETKF_ECUDA;
+    // one launch over both filters' domains: filter a writes the caller's buffer, filter b its own
+    FusedFrame f[2] = {{a, y_dev, sigma, xpred_dev, 1}, {b, y_dev, sigma, b->pair_pred, 1}};
+    prof_begin(a, STAGE_FUSED);
+    int rc = fused_batch(f, 2, a->d_queue, a->stream);
+    prof_end(a);
+    if (rc) return rc;
+    const int n = a->n_act;
+    pair_mean_kernel<<<(n + 255) / 256, 256, 0, a->stream>>>(static_cast<const float*>(xpred_dev),
+                                                              static_cast<const float*>(b->pair_pred),
+                                                              static_cast<float*>(xpred_dev), n);
+    if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
+    for (letkf_ctx* c : {a, b}) {
+        c->cur ^= 1;
+        c->frame += 1;
+        c->phase = 0;
+    }
+    return LETKF_OK;
+}
+
+extern "C" int letkf_set_capture(letkf_ctx* c, int domain, float* cap_dev, long long cap_floats) {
+    using namespace letkf;
+    if (!c) return LETKF_EINVAL;
+    if (c->path != LETKF_PATH_FUSED) return LETKF_ESTATE;
+    if (!cap_dev) {
+        c->cap_dev = nullptr;
+        c->cap_dom = -1;
+        return LETKF_OK;
+    }
+    const long long m = c->m, q = std::max(c->host.p_loc_max, 1);
+    if (domain < 0 || domain >= c->n_dom || cap_floats < CAP_HDR + m + std::max(m * m, 2 * q * m))
+        return LETKF_EINVAL;
+    c->cap_dev = cap_dev;
+    c->cap_dom = domain;
+    return LETKF_OK;
 }
 
 extern "C" int letkf_wait_selftest(long long limit_cycles, int arrive, void* stream) {

@@ -6,7 +6,8 @@
 // corners of valid subapertures.  Domains (Sect. 2.3): dom_sub x dom_sub blocks
 // of subapertures own their actuators (the last actuator row and column fold
 // into the last block); a domain observes the valid subapertures of its block
-// grown by `halo` subapertures, both slope directions.
+// grown by `halo` subapertures, both slope directions.  The block grid may be
+// shifted by dom_offset subapertures (the second partition of Sect. 5).
 
 #include <cmath>
 #include <cstdio>
@@ -54,7 +55,7 @@ std::vector<uint8_t> pupil_mask(int n, double obstruction) {
     return mask;
 }
 
-void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obstruction, int b, int halo) {
+void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obstruction, int b, int halo, int off) {
     h.n_sub = n;
     if (sub_valid) {
         h.sub_valid.assign(sub_valid, sub_valid + (size_t)n * n);
@@ -93,7 +94,9 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
     h.n_subv = (int)(h.sub_rc.size() / 2);
     h.n_act = (int)(h.act_rc.size() / 2);
 
-    const int nb = (n + b - 1) / b;
+    // block I spans subaperture rows [b I - off, b (I + 1) - off); the actuator row n folds into
+    // the block of subaperture row n - 1
+    const int nb = (n + off + b - 1) / b, last = (n - 1 + off) / b;
     h.own_off = {0};
     h.obs_off = {0};
     h.halo_off = {0};
@@ -105,9 +108,9 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
         for (int J = 0; J < nb; ++J) {
             std::vector<int> owned;
             for (int r = 0; r <= n; ++r) {
-                if (std::min(r / b, nb - 1) != I) continue;
+                if (std::min((r + off) / b, last) != I) continue;
                 for (int c = 0; c <= n; ++c) {
-                    if (std::min(c / b, nb - 1) != J) continue;
+                    if (std::min((c + off) / b, last) != J) continue;
                     const int k = h.act_index[(size_t)r * na + c];
                     if (k >= 0) owned.push_back(k);
                 }
@@ -115,8 +118,8 @@ void build_model(HostModel& h, int n, const unsigned char* sub_valid, double obs
             if (owned.empty()) continue;
             std::sort(owned.begin(), owned.end());
             std::vector<int> subs;
-            for (int r = std::max(0, b * I - halo); r < std::min(n, b * (I + 1) + halo); ++r)
-                for (int c = std::max(0, b * J - halo); c < std::min(n, b * (J + 1) + halo); ++c) {
+            for (int r = std::max(0, b * I - off - halo); r < std::min(n, b * (I + 1) - off + halo); ++r)
+                for (int c = std::max(0, b * J - off - halo); c < std::min(n, b * (J + 1) - off + halo); ++c) {
                     const int k = h.sub_index[(size_t)r * n + c];
                     if (k >= 0) subs.push_back(k);
                 }
@@ -226,9 +229,9 @@ bool tables_in_bounds(const HostModel& h) {
 // The geometry and domains of these parameters (the global path: one domain, no halo).
 void build_for(HostModel& h, const letkf_params* p) {
     if (p->path == LETKF_PATH_GLOBAL)
-        build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->n_sub, 0);
+        build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->n_sub, 0, 0);
     else
-        build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo);
+        build_model(h, p->n_sub, p->sub_valid, p->obstruction, p->dom_sub, p->halo, p->dom_offset);
 }
 
 void free_all(letkf_ctx* c) {
@@ -237,20 +240,18 @@ void free_all(letkf_ctx* c) {
                     c->tab.obs_sub, c->tab.obs_corner, c->tab.halo_off, c->tab.halo, c->tab.order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (c->cublas) cublasDestroy(c->cublas);
-    if (c->cublas_side) cublasDestroy(c->cublas_side);
     for (int b = 0; b < 2; ++b) {
         if (c->Vbuf[b]) cudaFree(c->Vbuf[b]);
         if (c->ev_v_ready[b]) cudaEventDestroy(c->ev_v_ready[b]);
         if (c->ev_v_used[b]) cudaEventDestroy(c->ev_v_used[b]);
     }
     if (c->Xi_side) cudaFree(c->Xi_side);
+    if (c->pair_pred) cudaFree(c->pair_pred);
     if (c->scratch) cudaFree(c->scratch);
     letkf::fused_graph_reset(c);
     letkf::global_free(c);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->cublas_cap) cublasDestroy(c->cublas_cap);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
@@ -272,7 +273,8 @@ int validate(const letkf_params* p) {
         !(p->ar2_a - p->ar1_a < 1.0) || (p->obs_block != 0 && p->obs_block != 1) ||
         p->precision < 0 || p->precision > 2 || p->path < 0 || p->path > 1 || p->q_white < 0 ||
         !(p->obstruction >= 0 && p->obstruction < 1) || p->piston < LETKF_PISTON_OFF ||
-        p->piston > LETKF_PISTON_IN_LOOP || p->simt_q_max > 128)
+        p->piston > LETKF_PISTON_IN_LOOP || p->simt_q_max > 128 || p->dom_offset < 0 ||
+        p->dom_offset >= p->dom_sub)
         return LETKF_EINVAL;
     if (p->precision == LETKF_PREC_FP64 && p->path != LETKF_PATH_PLAIN) return LETKF_EINVAL;
     if (p->precision == LETKF_PREC_MIXED && p->path != LETKF_PATH_FUSED) return LETKF_EINVAL;
@@ -302,6 +304,7 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
         const size_t vbytes = na * m_pad * 4;
         b += 2 * vbytes + (p->precision == LETKF_PREC_MIXED ? letkf::noise_xi_bytes(h.n_act, p->m)
                                                              : vbytes);
+        b += na * 4;            // the second filter's prediction of letkf_step_pair
         if (p->m + 1 > 128) {   // dual form: per-CTA halo anomalies
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) sms = 0;
@@ -359,8 +362,6 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     if ((rc = alloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
     if ((rc = alloc(c, (void**)&c->d_frame_bad, sizeof(int)))) return rc;
     if ((rc = alloc(c, (void**)&c->d_queue, 4 * sizeof(int)))) return rc;
-    if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
-    if (cublasSetStream(c->cublas, c->stream) != CUBLAS_STATUS_SUCCESS) return LETKF_ECUDA;
     if (c->path == LETKF_PATH_GLOBAL) {
         // buffers after the initial ensemble (they need the device noise factor)
     } else if (c->path == LETKF_PATH_PLAIN) {
@@ -380,9 +381,9 @@ int create_impl(const letkf_params* p, letkf_ctx* c) {
     } else {
         if ((rc = letkf::fused_prepare(c))) return rc;
     }
+    c->lq_lower = p->q_sqrt && letkf::lower_triangular(p->q_sqrt, c->n_act);
     if ((rc = letkf::init_ensemble(c, p->q_sqrt, p->p0_sqrt))) return rc;
     if ((rc = letkf::piston_prepare(c))) return rc;
-    c->lq_lower = p->q_sqrt && letkf::lower_triangular(p->q_sqrt, c->n_act);
     if (c->path == LETKF_PATH_GLOBAL && (rc = letkf::global_prepare(c))) return rc;
     CU(cudaStreamSynchronize(c->stream));
     c->cur = 0;
@@ -744,7 +745,7 @@ const char* letkf_status_string(int s) {
         case LETKF_OK: return "ok";
         case LETKF_EINVAL: return "invalid argument or unsupported configuration";
         case LETKF_ENOMEM: return "out of memory";
-        case LETKF_ECUDA: return "CUDA or cuBLAS call failed";
+        case LETKF_ECUDA: return "CUDA runtime call failed";
         case LETKF_ETIMEOUT: return "a bounded device-side wait gave up";
         case LETKF_ENONFINITE: return "non-finite slopes: frame rejected, state unchanged";
         case LETKF_ESTATE: return "call out of order";

@@ -1,7 +1,6 @@
 // Internal definitions shared by the host code and the kernel files of libletkf.
 #pragma once
 
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -79,7 +78,6 @@ struct letkf_ctx {
     void* noise_part = nullptr;     // partial sums of row blocks split over several items
     int noise_nb = 0, noise_np = 0, noise_tile_b = 0, noise_n_items = 0, noise_grid = 0, noise_n_rb = 0;
     void* V = nullptr;              // perturbations, n_act x m_pad (state type)
-    cublasHandle_t cublas = nullptr;
     // scratch of the plain path
     void* S = nullptr;              // observed anomalies / sigma, sum(p_loc) x m_pad
     void* dt = nullptr;             // innovations / sigma, sum(p_loc)
@@ -101,7 +99,6 @@ struct letkf_ctx {
     // fused path: process noise of the next frame drawn on a side stream while the current
     // frame's kernel runs (double-buffered; v_frame[b] = frame whose draw buffer b holds)
     cudaStream_t side = nullptr;
-    cublasHandle_t cublas_side = nullptr;
     cudaEvent_t ev_v_ready[2] = {nullptr, nullptr};
     cudaEvent_t ev_v_used[2] = {nullptr, nullptr};
     void* Vbuf[2] = {nullptr, nullptr};
@@ -117,7 +114,6 @@ struct letkf_ctx {
     int gcur[2] = {-1, -1};
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t cap_stream = nullptr;      // capture only
-    cublasHandle_t cublas_cap = nullptr;
     // global path (one domain, tiled tensor-core products)
     letkf::GlobalState* gstate = nullptr;
     int lq_lower = 0;               // the process-noise factor is lower triangular
@@ -132,6 +128,12 @@ struct letkf_ctx {
     void* pst_K = nullptr;
     void* pst_g = nullptr;
     void* xhat = nullptr;
+    // fused path, test instrument: the analysis of domain cap_dom writes its mean weights and
+    // transform (or the transform's factors) to cap_dev (letkf_set_capture)
+    float* cap_dev = nullptr;
+    int cap_dom = -1;
+    // fused path: this context's prediction when it is the second filter of letkf_step_pair
+    void* pair_pred = nullptr;
     // stage timing
     int prof_on = 0;
     std::vector<int> prof_stage;            // stage of each record
@@ -158,9 +160,8 @@ size_t plain_smem_bytes(const letkf_ctx* c, int which);
 int launch_precheck(letkf_ctx* c, const void* y);
 int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analysis);
 int draw_perturbations(letkf_ctx* c, unsigned long long frame);
-// Normals of `frame` into xi, then V = L xi into v_out, on `stream` with `handle`.
-int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream,
-                          cublasHandle_t handle);
+// Normals of `frame` into xi, then V = L xi into v_out, on `stream`.
+int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream);
 int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host);
 // Node parameters of the normals kernel draw_perturbations_on launches (arguments held in *nn).
 struct NormalsNode {
@@ -244,7 +245,7 @@ int noise_prepare(letkf_ctx* c, const double* L_host);
 int noise_draw(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream);
 // The product part of noise_draw / draw_perturbations_on (normals already in xi).
 int noise_product(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream);
-int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream, cublasHandle_t handle);
+int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream);
 int noise_normals_params(letkf_ctx* c, unsigned long long frame, void* xi, NormalsNode* nn);
 int launch_copy_rows(letkf_ctx* c, const void* src, void* dst);
 

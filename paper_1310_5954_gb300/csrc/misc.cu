@@ -3,8 +3,9 @@
 // Forecast (Sect. 2.1): A1 = [[a I, 0], [I, 0]] on the two-instant state, so per
 // member: second instant <- first, first <- a * first + v.  The perturbation is
 // v = L xi with xi counter-based Philox4x32-10 normals (stream 1, frame k); with
-// a dense L the product is one GEMM per frame (cuBLAS: FP64 / FP32 / BF16 inputs
-// with FP32 accumulation, by precision), with white noise it is drawn inline.
+// a dense L the product is one GEMM per frame (FP64 / FP32: row_gemm_kernel below on the
+// CUDA cores; mixed precision: the BF16 tensor-core kernel of noise.cu), with white noise it is
+// drawn inline.
 
 #include <cuda_runtime.h>
 
@@ -135,23 +136,92 @@ int grid_for(size_t work, int block) {
     return (int)g;
 }
 
-// FP64 / FP32: V (n_act x m, ld m_pad) = L (n_act x n_act, row-major) * Xi (n_act x m, ld xld).
-// Column-major view used by cuBLAS: V^T = Xi^T L^T.  (Mixed precision uses noise.cu.)
-int noise_gemm(letkf_ctx* c, const void* L, const void* Xi, int xld, int gemm_type, void* V) {
-    const int m = c->m, na = c->n_act;
-    cublasStatus_t st;
-    if (gemm_type == 0) {
-        const double one = 1.0, zero = 0.0;
-        st = cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, (const double*)Xi, xld,
-                         (const double*)L, na, &zero, (double*)V, c->m_pad);
-    } else if (gemm_type == 1) {
-        const float one = 1.f, zero = 0.f;
-        st = cublasSgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, na, na, &one, (const float*)Xi, xld,
-                         (const float*)L, na, &zero, (float*)V, c->m_pad);
-    } else {
-        return LETKF_EINVAL;
+// V (n x m, row stride ldv) = L (n x n, row-major) * Xi (n x m, row stride ldx), in the state type
+// on the CUDA cores.  A CTA computes a 64 x 64 tile of V: 256 threads, each a 4 x 4 register block
+// (rows ty + 16 i, columns tx + 16 j, so that a warp's shared-memory reads hit distinct banks),
+// over K steps of 16 staged in shared memory, the next step's tile prefetched into registers while
+// the current one is multiplied.  With a lower-triangular L the K loop of a row block stops at its
+// last row (the zero upper triangle is never read).  Every sum runs over k in increasing order.
+constexpr int RG_BM = 64, RG_BN = 64, RG_BK = 16, RG_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(RG_THREADS) row_gemm_kernel(const T* __restrict__ L, const T* __restrict__ Xi,
+                                                              T* __restrict__ V, int n, int m, int ldx, int ldv,
+                                                              int lower) {
+    __shared__ T As[RG_BK][RG_BM + 1];   // As[k][row]: L tile, transposed
+    __shared__ T Bs[RG_BK][RG_BN];       // Bs[k][col]: Xi tile
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int r0 = blockIdx.x * RG_BM, c0 = blockIdx.y * RG_BN;
+    const int kend = lower ? min(n, r0 + RG_BM) : n;
+    // loads: A, 64 rows x 16 k, thread -> row tid / 4, k 4 (tid % 4) .. + 3;
+    //        B, 16 k x 64 columns, thread -> k tid / 16, columns 4 (tid % 16) .. + 3
+    const int ar = tid >> 2, ak = 4 * (tid & 3);
+    const int bk = tid >> 4, bc = 4 * (tid & 15);
+    T ra[4], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + ar, k = k0 + ak + u;
+            ra[u] = (r < n && k < kend) ? L[(size_t)r * n + k] : T(0);
+            const int kk = k0 + bk, cc = c0 + bc + u;
+            rb[u] = (kk < kend && cc < m) ? Xi[(size_t)kk * ldx + cc] : T(0);
+        }
+    };
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    if (kend > 0) fetch(0);
+    for (int k0 = 0; k0 < kend; k0 += RG_BK) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            As[ak + u][ar] = ra[u];
+            Bs[bk][bc + u] = rb[u];
+        }
+        __syncthreads();
+        if (k0 + RG_BK < kend) fetch(k0 + RG_BK);
+#pragma unroll
+        for (int k = 0; k < RG_BK; ++k) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
     }
-    return st == CUBLAS_STATUS_SUCCESS ? LETKF_OK : LETKF_ECUDA;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty + 16 * i;
+        if (r >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cc = c0 + tx + 16 * j;
+            if (cc < m) V[(size_t)r * ldv + cc] = acc[i][j];
+        }
+    }
+}
+
+// FP64 / FP32: V (n_act x m, ld m_pad) = L (n_act x n_act, row-major) * Xi (n_act x m, ld xld) on
+// `stream`.  (Mixed precision uses noise.cu.)
+int noise_gemm(letkf_ctx* c, const void* L, const void* Xi, int xld, int gemm_type, void* V, cudaStream_t stream,
+               bool lower) {
+    const int m = c->m, na = c->n_act;
+    const dim3 grid((na + RG_BM - 1) / RG_BM, (m + RG_BN - 1) / RG_BN);
+    if (gemm_type == 0)
+        row_gemm_kernel<double><<<grid, RG_THREADS, 0, stream>>>((const double*)L, (const double*)Xi, (double*)V, na,
+                                                                 m, xld, c->m_pad, lower ? 1 : 0);
+    else if (gemm_type == 1)
+        row_gemm_kernel<float><<<grid, RG_THREADS, 0, stream>>>((const float*)L, (const float*)Xi, (float*)V, na, m,
+                                                                xld, c->m_pad, lower ? 1 : 0);
+    else
+        return LETKF_EINVAL;
+    return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
 }
 
 int gemm_type_of(const letkf_ctx* c) {
@@ -182,11 +252,10 @@ int draw_perturbations(letkf_ctx* c, unsigned long long frame) {
 }
 
 int draw_perturbations_impl(letkf_ctx* c, unsigned long long frame) {
-    return draw_perturbations_on(c, frame, c->Xi, c->V, c->stream, c->cublas);
+    return draw_perturbations_on(c, frame, c->Xi, c->V, c->stream);
 }
 
-int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream,
-                          cublasHandle_t handle) {
+int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream) {
     if (c->Lt) return noise_draw(c, frame, xi, v_out, stream);
     const int gt = gemm_type_of(c);
     const int nq = (c->n_act + 3) / 4;
@@ -198,20 +267,12 @@ int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void
         normals_kernel<float><<<g, 256, 0, stream>>>((float*)xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
                                                      (uint32_t)frame);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
-    cublasHandle_t saved = c->cublas;
-    c->cublas = handle;
-    const int rc = noise_gemm(c, c->Lq, xi, c->m_pad, gt, v_out);
-    c->cublas = saved;
-    return rc;
+    return noise_gemm(c, c->Lq, xi, c->m_pad, gt, v_out, stream, c->lq_lower != 0);
 }
 
-int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream, cublasHandle_t handle) {
+int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream) {
     if (c->Lt) return noise_product(c, xi, v_out, stream);
-    cublasHandle_t saved = c->cublas;
-    c->cublas = handle;
-    const int rc = noise_gemm(c, c->Lq, xi, c->m_pad, gemm_type_of(c), v_out);
-    c->cublas = saved;
-    return rc;
+    return noise_gemm(c, c->Lq, xi, c->m_pad, gemm_type_of(c), v_out, stream, c->lq_lower != 0);
 }
 
 // Kernel-node parameters of the normals launch draw_perturbations_on makes for `frame` into xi
@@ -336,6 +397,8 @@ int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
         return LETKF_OK;
     };
     int rc = LETKF_OK;
+    // the stationary factor is lower triangular when given as a Cholesky factor, or when it is L scaled
+    const bool p0_lower = P0_host ? lower_triangular(P0_host, na) : c->lq_lower != 0;
     if (cudaMalloc(&xi, (size_t)na * row) != cudaSuccess) return LETKF_ENOMEM;
     cudaMemset(xi, 0, (size_t)na * row);
     // stationary standard deviation of the AR model with unit innovations (the default P0 scale):
@@ -360,15 +423,15 @@ int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
             if ((rc = upload_conv(L_host, sa, &Pf))) goto done;
         }
         draw(0);
-        if ((rc = noise_gemm(c, Pf, xi, c->m_pad, gt, X2))) goto done;
+        if ((rc = noise_gemm(c, Pf, xi, c->m_pad, gt, X2, c->stream, p0_lower))) goto done;
         draw(1);
-        if ((rc = noise_gemm(c, Lf, xi, c->m_pad, gt, X))) goto done;  // first rows <- L xi1
+        if ((rc = noise_gemm(c, Lf, xi, c->m_pad, gt, X, c->stream, c->lq_lower != 0))) goto done;  // first rows <- L xi1
     } else {
         // white noise: second = (q / sqrt(1 - a^2)) xi0 (or P0 xi0), first = a second + q xi1
         if (P0_host) {
             if ((rc = upload_conv(P0_host, 1.0, &Pf))) goto done;
             draw(0);
-            if ((rc = noise_gemm(c, Pf, xi, c->m_pad, gt, X2))) goto done;
+            if ((rc = noise_gemm(c, Pf, xi, c->m_pad, gt, X2, c->stream, p0_lower))) goto done;
         } else {
             draw(0);
             cudaMemcpyAsync(X2, xi, (size_t)na * row, cudaMemcpyDeviceToDevice, c->stream);

@@ -375,6 +375,32 @@ __global__ void __launch_bounds__(kThreads) plain_transform(const T* __restrict_
     }
 }
 
+// The four analysis kernels take dynamic shared memory sized by the system (ensemble, domain
+// sizes).  Their limit is raised once per device and state type, with that device current, to
+// all the shared memory a block may opt in to (less the kernel's static shared memory), so that
+// no context's setting can later lower it below another's needs; every call is checked.
+template <typename T>
+int plain_kernels_ready(int device) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) return LETKF_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[device]) return LETKF_OK;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return LETKF_ECUDA;
+    const void* fns[4] = {reinterpret_cast<const void*>(plain_obs<T>), reinterpret_cast<const void*>(plain_gram<T>),
+                          reinterpret_cast<const void*>(plain_eig<T>), reinterpret_cast<const void*>(plain_transform<T>)};
+    for (const void* fn : fns) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return LETKF_ECUDA;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) !=
+            cudaSuccess)
+            return LETKF_ECUDA;
+    }
+    done[device] = true;
+    return LETKF_OK;
+}
+
 template <typename T>
 int plain_analyze_t(letkf_ctx* c, const T* y, double sigma) {
     if (sigma > 0) c->sigma = sigma;
@@ -389,10 +415,7 @@ int plain_analyze_t(letkf_ctx* c, const T* y, double sigma) {
     const int M = m + (m & 1);
     const size_t sm_eig = (size_t)2 * M * (M + 1) * sizeof(T) + (size_t)3 * M * sizeof(T) + (size_t)M * sizeof(int);
     const size_t sm_tr = ((size_t)m * m + (size_t)c->host.n_loc_max * (m + 1)) * sizeof(T);
-    cudaFuncSetAttribute(plain_obs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_obs);
-    cudaFuncSetAttribute(plain_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram);
-    cudaFuncSetAttribute(plain_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_eig);
-    cudaFuncSetAttribute(plain_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tr);
+    if ((rc = plain_kernels_ready<T>(c->device))) return rc;
     prof_begin(c, STAGE_OBS);
     plain_obs<T><<<nd, kThreads, sm_obs, c->stream>>>(X, y, c->tab, c->so_off, static_cast<T*>(c->S),
                                                       static_cast<T*>(c->dt), m, mp, row0, c->n_subv,
@@ -518,10 +541,7 @@ int analyze_static_t(letkf_ctx* c, const T* y, double sigma, T* out) {
     const int M = m + (m & 1);
     const size_t sm_eig = (size_t)2 * M * (M + 1) * sizeof(T) + (size_t)3 * M * sizeof(T) + (size_t)M * sizeof(int);
     const size_t sm_tr = ((size_t)m * m + (size_t)c->host.n_loc_max * (m + 1)) * sizeof(T);
-    cudaFuncSetAttribute(plain_obs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_obs);
-    cudaFuncSetAttribute(plain_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram);
-    cudaFuncSetAttribute(plain_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_eig);
-    cudaFuncSetAttribute(plain_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tr);
+    if ((rc = plain_kernels_ready<T>(c->device))) return rc;
     static_check_kernel<T><<<1, 1024, 0, c->stream>>>(y, c->p, flag, c->d_status);
     plain_obs<T><<<nd, kThreads, sm_obs, c->stream>>>(X, y, c->tab, c->so_off, S, dt, m, mp, row0, c->n_subv,
                                                       (T)(1.0 / sg), flag);

@@ -43,7 +43,8 @@ struct System {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;      // the batch's first operation on the stream (device clock)
+    cudaEvent_t done = nullptr;       // its last
     int* queue = nullptr;             // 4 ints: the fused kernel's work-queue counters
     bool busy = false;
     long long t_launch = 0;
@@ -60,6 +61,7 @@ long long now_ns() {
 
 struct letkf_server {
     letkf_server_params prm{};
+    cudaEvent_t ref = nullptr;        // device-clock origin of the records' device times
     unsigned long long used = 0;
     std::vector<System> sys;
     std::vector<Slot> slots;
@@ -95,6 +97,11 @@ int retire(letkf_server* S) {
         if (q == cudaErrorNotReady) continue;
         if (q != cudaSuccess) return LETKF_ECUDA;
         const long long t = now_ns();
+        // device-clock interval of the batch, relative to the server's reference event
+        float ms0 = 0.f, ms1 = 0.f;
+        if (cudaEventElapsedTime(&ms0, S->ref, sl.start) != cudaSuccess ||
+            cudaEventElapsedTime(&ms1, S->ref, sl.done) != cudaSuccess)
+            return LETKF_ECUDA;
         for (int id : sl.systems) {
             System& s = S->sys[id];
             letkf_frame_record r;
@@ -106,6 +113,8 @@ int retire(letkf_server* S) {
             r.t_done_ns = t;
             r.batch_systems = (int)sl.systems.size();
             r.slot = (int)k;
+            r.t_dev_start_ns = (long long)((double)ms0 * 1e6);
+            r.t_dev_end_ns = (long long)((double)ms1 * 1e6);
             S->records.push_back(r);
             if (s.out && s.out_frames > 0)
                 std::memcpy(s.out + (size_t)(s.inflight_frame % (unsigned long long)s.out_frames) * s.n_act,
@@ -143,6 +152,7 @@ int launch(letkf_server* S) {
     });
     if ((int)ready.size() > S->prm.max_batch) ready.resize(S->prm.max_batch);
     Slot& sl = S->slots[k];
+    if (cudaEventRecord(sl.start, sl.stream) != cudaSuccess) return LETKF_ECUDA;
     std::vector<letkf::FusedFrame> frames;
     for (int id : ready) {
         System& s = S->sys[id];
@@ -218,7 +228,7 @@ int letkf_server_create(const letkf_server_params* p, letkf_server** out) {
     int rc = LETKF_OK;
     for (Slot& sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreate(&sl.start) != cudaSuccess || cudaEventCreate(&sl.done) != cudaSuccess) {
             rc = LETKF_ECUDA;
             break;
         }
@@ -227,6 +237,9 @@ int letkf_server_create(const letkf_server_params* p, letkf_server** out) {
             break;
         }
     }
+    if (!rc && (cudaEventCreate(&S->ref) != cudaSuccess || cudaEventRecord(S->ref, S->slots[0].stream) != cudaSuccess ||
+                cudaEventSynchronize(S->ref) != cudaSuccess))
+        rc = LETKF_ECUDA;
     if (rc) {
         letkf_server_destroy(S);
         return rc;
@@ -244,9 +257,11 @@ int letkf_server_destroy(letkf_server* S) {
         if (s.used) drop_system(s);
     for (Slot& sl : S->slots) {
         if (sl.queue) cudaFree(sl.queue);
+        if (sl.start) cudaEventDestroy(sl.start);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (S->ref) cudaEventDestroy(S->ref);
     delete S;
     return LETKF_OK;
 }

@@ -25,12 +25,13 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
                 obstruction: float = 0.0, sub_valid: Optional[np.ndarray] = None,
                 q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0, p0_sqrt: Optional[np.ndarray] = None,
                 precision: str = "fp32", path: str = "plain", seed: int = 0, obs_block: int = 1,
-                ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0):
+                ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0, dom_offset: int = 0):
     """letkf_params for the C ABI, and the host arrays it points to (keep them alive while it is used).
 
     piston: "off", "output" or "in_loop" (differential-piston removal between domains);
     simt_q_max: fused path, domains with min(p_loc, m) <= this take the FP32 analysis on the CUDA
-    cores (0: the library default, negative: every domain on the tensor cores).
+    cores (0: the library default, negative: every domain on the tensor cores);
+    dom_offset: shift of the domains' block grid in subapertures (0 <= dom_offset < dom_sub).
     """
     p = _lib.letkf_params()
     keep = []
@@ -63,6 +64,7 @@ def make_params(n_sub: int, m: int, ar1_a: float, sigma: float, dom_sub: int = 4
         raise ValueError(f"piston must be one of {sorted(_PISTON)}")
     p.piston = _PISTON[piston]
     p.simt_q_max = int(simt_q_max)
+    p.dom_offset = int(dom_offset)
     return p, keep
 
 
@@ -80,7 +82,7 @@ class LETKF:
                  q_sqrt: Optional[np.ndarray] = None, q_white: float = 0.0,
                  p0_sqrt: Optional[np.ndarray] = None, precision: str = "fp32", path: str = "plain",
                  seed: int = 0, obs_block: int = 1, device: Optional[int] = None, stream=None,
-                 ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0):
+                 ar2_a: float = 0.0, piston: str = "off", simt_q_max: int = 0, dom_offset: int = 0):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -91,7 +93,7 @@ class LETKF:
         p, keep = make_params(n_sub=n_sub, m=m, ar1_a=ar1_a, sigma=sigma, dom_sub=dom_sub, halo=halo,
                               obstruction=obstruction, sub_valid=sub_valid, q_sqrt=q_sqrt, q_white=q_white,
                               p0_sqrt=p0_sqrt, precision=precision, path=path, seed=seed, obs_block=obs_block,
-                              ar2_a=ar2_a, piston=piston, simt_q_max=simt_q_max)
+                              ar2_a=ar2_a, piston=piston, simt_q_max=simt_q_max, dom_offset=dom_offset)
         self._keep = keep
         p.device = dev
         p.stream = self.stream.cuda_stream
@@ -161,6 +163,39 @@ class LETKF:
         """Global path: (Newton-Schulz steps, spectral bound s) of the last analysis."""
         return _lib.letkf_global_stats(self.ctx)
 
+    def capture_transform(self, domain: Optional[int]):
+        """Fused path, test instrument: from the next analysis on, domain `domain` (numbering of
+        letkf_domain_tables) writes its mean weights and transform into a device buffer, which
+        `captured()` reads; None stops it."""
+        import torch
+        if domain is None:
+            _lib.letkf_set_capture(self.ctx, -1, 0, 0)
+            self._cap = None
+            return
+        i = self.info
+        n = 8 + i.m + max(i.m * i.m, 2 * max(i.p_loc_max, 1) * i.m)
+        self._cap = torch.zeros(n, dtype=torch.float32, device=self.device)
+        _lib.letkf_set_capture(self.ctx, int(domain), self._cap.data_ptr(), n)
+
+    def captured(self) -> dict:
+        """The captured domain's last analysis: form ("mm" or "dual", "tensor" or "simt"), the
+        conditioning bound s, the Newton-Schulz steps, w_bar (m) and T (m x m; for the dual forms
+        T = I - W^T M from the captured W and M = (I + Z)^-1 W, formed here in float64)."""
+        self.sync()
+        c = self._cap.cpu().numpy().astype(np.float64)
+        form, q, s, it = int(c[0]), int(c[1]), c[2], int(c[3])
+        m = self.info.m
+        wbar = c[8:8 + m].copy()
+        if form in (0, 2):
+            T = c[8 + m:8 + m + m * m].reshape(m, m).copy()
+            W = M = None
+        else:
+            W = c[8 + m:8 + m + q * m].reshape(q, m).copy()
+            M = c[8 + m + q * m:8 + m + 2 * q * m].reshape(q, m).copy()
+            T = np.eye(m) - W.T @ M
+        return {"form": ("mm" if form in (0, 2) else "dual") + ("/tensor" if form in (0, 1) else "/simt"),
+                "q": q, "s": s, "ns_steps": it, "wbar": wbar, "T": T, "W": W, "M": M}
+
     def set_graph(self, enable: bool) -> None:
         """Fused path: run each step as one CUDA graph launch, or as separate launches (default)."""
         _lib.letkf_set_graph(self.ctx, 1 if enable else 0)
@@ -219,3 +254,37 @@ class LETKF:
             self.close()
         except Exception:
             pass
+
+
+class LETKFPair:
+    """Two local ETKFs run together on the same slopes with two domain partitions (Sect. 5): the
+    second filter's block grid is shifted by `offset` subapertures (default dom_sub // 2) and its
+    noise streams by its seed (default seed + 1); each step returns the mean of the two filters'
+    predictions (letkf_step_pair).  Keyword arguments as for LETKF (fused path)."""
+
+    def __init__(self, offset: Optional[int] = None, seed_b: Optional[int] = None, **kw):
+        kw = dict(kw)
+        kw["path"] = "fused"
+        dom_sub = kw.get("dom_sub", 4)
+        off = dom_sub // 2 if offset is None else int(offset)
+        seed = int(kw.get("seed", 0))
+        self.a = LETKF(**dict(kw, dom_offset=0))
+        self.b = LETKF(**dict(kw, dom_offset=off, seed=seed + 1 if seed_b is None else int(seed_b),
+                              stream=self.a.stream))
+        self.info, self.dtype, self.device, self.stream = self.a.info, self.a.dtype, self.a.device, self.a.stream
+
+    def step(self, y, sigma: float = 0.0, out=None):
+        """One frame of both filters; returns the mean of their x_hat(k+1|k) (n_act)."""
+        if out is None:
+            out = self.a._torch.empty(self.info.n_act, dtype=self.dtype, device=self.device)
+        _lib.letkf_step_pair(self.a.ctx, self.b.ctx, self.a._dev(y, self.info.p, "y"), sigma,
+                             self.a._dev(out, self.info.n_act, "out"))
+        return out
+
+    def sync(self) -> int:
+        ra, rb = self.a.sync(), self.b.sync()
+        return ra or rb
+
+    def close(self) -> None:
+        self.a.close()
+        self.b.close()

@@ -53,3 +53,28 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def domain_errors(xa, xo, doms, n_act):
+    """Per domain: relative L2 error of its owned rows' analysis mean and of their anomalies
+    (members minus that mean), GPU against oracle, over both state instants."""
+    out = []
+    for d in doms:
+        r = d.rows(n_act)
+        ma, mo = xa[r].mean(1), xo[r].mean(1)
+        out.append((rel(ma, mo), rel(xa[r] - ma[:, None], xo[r] - mo[:, None])))
+    return out
+
+
+def assert_domainwise(xa, xo, doms, n_act, tol_mean, tol_anom, tag=""):
+    """Every domain within the bounds; a failure names the worst domain (block, slopes, rows)."""
+    xa = np.asarray(xa, dtype=np.float64)
+    xo = np.asarray(xo, dtype=np.float64)
+    errs = domain_errors(xa, xo, doms, n_act)
+    for which, tol, name in ((0, tol_mean, "analysis mean"), (1, tol_anom, "anomalies")):
+        k = max(range(len(errs)), key=lambda i: errs[i][which])
+        d = doms[k]
+        assert errs[k][which] < tol, (
+            f"{tag}: {name} of domain {k} (block {d.I},{d.J}, p_loc {2 * d.obs_sub.size}, "
+            f"n_loc {2 * d.owned_act.size}) off by {errs[k][which]:.3e} relative (bound {tol:.1e})")
+    return errs

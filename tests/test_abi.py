@@ -69,6 +69,8 @@ def test_null_arguments(lib):
     assert lib.letkf_global_stats(None, ctypes.byref(n), ctypes.byref(sb)) == _lib.LETKF_EINVAL
     nd = ctypes.c_int()
     assert lib.letkf_piston_operator(None, None, ctypes.byref(nd)) == _lib.LETKF_EINVAL
+    assert lib.letkf_set_capture(None, 0, None, 0) == _lib.LETKF_EINVAL
+    assert lib.letkf_step_pair(None, None, None, 0.0, None) == _lib.LETKF_EINVAL
 
 
 def test_gemm_selftest_rejects_bad_shapes(lib):
@@ -171,3 +173,33 @@ def test_headers_are_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-fsyntax-only", str(src)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("n,obs,b,h,off", [(8, 0.0, 4, 1, 2), (40, 0.14, 4, 2, 2), (80, 0.28, 4, 2, 2),
+                                           (13, 0.2, 4, 2, 3), (40, 0.14, 4, 2, 0), (10, 0.0, 3, 1, 1)])
+def test_domain_tables_match_the_oracle_also_on_a_shifted_grid(lib, n, obs, b, h, off):
+    """The library's domains (letkf_domain_tables) equal the oracle's, for the block grid shifted by
+    dom_offset too (the second partition of Sect. 5)."""
+    from oracle import geometry
+    from paper_1310_5954_gb300.letkf import make_params
+    p, keep = make_params(n_sub=n, m=20, ar1_a=0.9, sigma=0.1, dom_sub=b, halo=h, obstruction=obs, q_white=0.1,
+                          precision="fp32", path="fused", dom_offset=off)
+    tab = _lib.letkf_domain_tables(p)
+    g = geometry.make_geometry(n, obs)
+    doms = {(d.I, d.J): d for d in geometry.make_domains(g, b, h, offset=off)}
+    nb = tab["blocks_per_side"]
+    assert tab["n_dom"] == len(doms) and tab["n_act"] == g.n_act
+    for k in range(tab["n_dom"]):
+        d = doms[divmod(int(tab["block"][k]), nb)]
+        own = tab["own"][tab["own_off"][k]:tab["own_off"][k + 1]]
+        obs_sub = tab["obs_sub"][tab["obs_off"][k]:tab["obs_off"][k + 1]]
+        assert np.array_equal(own, d.owned_act) and np.array_equal(obs_sub, d.obs_sub), k
+
+
+def test_domain_offset_outside_the_block_is_refused(lib):
+    from paper_1310_5954_gb300.letkf import make_params
+    for off in (-1, 4):
+        p, keep = make_params(n_sub=8, m=20, ar1_a=0.9, sigma=0.1, dom_sub=4, halo=1, q_white=0.1,
+                              precision="fp32", path="fused", dom_offset=off)
+        out = ctypes.c_void_p(1234)
+        assert lib.letkf_create(ctypes.byref(p), ctypes.byref(out)) == _lib.LETKF_EINVAL

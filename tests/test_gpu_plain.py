@@ -14,7 +14,7 @@ from oracle import etkf, philox
 from paper_1310_5954_gb300 import _lib
 from paper_1310_5954_gb300 import build as builder
 
-from _gpu_common import gpu_filter, model, oracle_filter, rel, slopes
+from _gpu_common import assert_domainwise, gpu_filter, model, oracle_filter, rel, slopes
 
 pytestmark = pytest.mark.gpu
 
@@ -92,6 +92,8 @@ def test_fp64_free_running_matches_oracle():
     x, frame = f.get_state()
     assert frame == n_frames
     assert rel(x.cpu().numpy(), o.X) < 1e-10
+    w, g, doms, _, _ = model("tiny-8x8")
+    assert_domainwise(x.cpu().numpy(), o.X, doms, g.n_act, 1e-9, 1e-9, tag="tiny plain fp64")
     assert f.sync() == 0
     f.close()
 
@@ -100,6 +102,7 @@ def test_fp64_free_running_matches_oracle():
 def test_fp32_single_frame_analysis(name, frames):
     """From the same FP32-representable forecast ensemble, one analysis on each side."""
     y, _ = slopes(name, frames + 1)
+    w, g, doms, _, _ = model(name)
     f = gpu_filter(name, "fp32", "plain")
     o = oracle_filter(name)
     for k in range(frames):
@@ -112,6 +115,8 @@ def test_fp32_single_frame_analysis(name, frames):
         xa = xa.cpu().numpy().astype(np.float64)
         assert rel(xa.mean(1), o.X.mean(1)) < 1e-4, k
         assert rel(xa, o.X) < 1e-3, k
+        # per domain, the cold-start bounds of the fused path (FP32 Jacobi: kappa 2^-24 in T)
+        assert_domainwise(xa, o.X, doms, g.n_act, 2e-3, 5e-3, tag=f"{name} plain fp32 frame {k}")
         f.forecast()
         o.forecast()
     assert f.sync() == 0

@@ -179,3 +179,60 @@ def test_replay_runs_a_trace_in_real_time():
     lat = np.array([r["t_done_ns"] - r["t_arrival_ns"] for r in recs])
     assert (lat > 0).all() and np.median(lat) < 50_000_000
     srv.close()
+
+
+def _overlapping_pairs(recs):
+    """Pairs of batches in different stream slots whose device-clock intervals intersect."""
+    batches = {}
+    for r in recs:
+        batches[(r["slot"], r["t_dev_start_ns"], r["t_dev_end_ns"])] = True
+    b = sorted(batches)
+    return [(x, y) for i, x in enumerate(b) for y in b[i + 1:]
+            if x[0] != y[0] and max(x[1], y[1]) < min(x[2], y[2])]
+
+
+def test_admission_while_frames_are_in_flight_and_overlap_on_the_device():
+    """Continuous batching: a system's frame is launched into the second stream slot while another
+    system's batch is still on the GPU, and a third system is admitted while a batch is outstanding
+    (no drain).  The two slots' batches overlap on the device clock (CUDA events), and every
+    system's predictions and final ensemble equal those of the same system stepped alone, bit for
+    bit."""
+    systems = [("elt-80x80", True, None), ("tiny-8x8", True, None), ("tiny-8x8", False, None)]
+    ys = [_frames(name) for name, _, _ in systems]
+    srv = Server(slots=2, max_pending=16)
+    ids = [srv.admit(**_kw(*systems[0])), srv.admit(**_kw(*systems[1]))]
+    outs = [srv.set_output(i, FRAMES) for i in ids]
+    in_flight_at_admission = -1
+    sent_c = 0
+    for k in range(FRAMES):
+        assert srv.submit(ids[0], ys[0][k]) == _lib.LETKF_OK
+        srv.pump()                                   # the large system's frame k on one slot
+        assert srv.submit(ids[1], ys[1][k]) == _lib.LETKF_OK
+        srv.pump()                                   # the small one's, while that batch runs
+        if k == 3:
+            in_flight_at_admission = srv.info()["frames_in_flight"]
+            ids.append(srv.admit(**_kw(*systems[2])))
+            outs.append(srv.set_output(ids[2], FRAMES))
+        if len(ids) == 3:
+            assert srv.submit(ids[2], ys[2][sent_c]) == _lib.LETKF_OK
+            sent_c += 1
+            srv.pump()
+    while sent_c < FRAMES:
+        assert srv.submit(ids[2], ys[2][sent_c]) == _lib.LETKF_OK
+        sent_c += 1
+    srv.drain()
+    states = [srv.state(i) for i in ids]
+    recs = srv.records()
+    srv.close()
+    assert in_flight_at_admission >= 1, "nothing was in flight when the third system was admitted"
+    assert all(r["status"] == _lib.LETKF_OK for r in recs) and len(recs) == 3 * FRAMES
+    for r in recs:
+        assert 0 <= r["t_dev_start_ns"] < r["t_dev_end_ns"]
+    pairs = _overlapping_pairs(recs)
+    assert pairs, "no two batches of different slots overlapped on the device"
+    for s, (name, dense, m) in enumerate(systems):
+        preds, x, frame, st = _alone(name, dense, m, ys[s])
+        assert st == 0
+        assert np.array_equal(outs[s], preds), (name, np.abs(outs[s] - preds).max())
+        assert np.array_equal(states[s][0].cpu().numpy(), x) and states[s][1] == frame == FRAMES
+        assert [r["frame"] for r in recs if r["system"] == ids[s]] == list(range(FRAMES))

@@ -142,23 +142,26 @@ def test_domain_statistics_of_the_workload_systems(key, want):
     assert got == want
 
 
-@pytest.mark.parametrize("n,obs,b,h", [(8, 0.0, 4, 1), (8, 0.0, 4, 0), (13, 0.2, 4, 2), (40, 0.14, 4, 2),
-                                       (80, 0.28, 4, 2), (10, 0.0, 3, 1), (9, 0.3, 5, 3)])
-def test_domains_equal_brute_force_membership(n, obs, b, h):
+@pytest.mark.parametrize("n,obs,b,h,off", [(8, 0.0, 4, 1, 0), (8, 0.0, 4, 0, 0), (13, 0.2, 4, 2, 0),
+                                           (40, 0.14, 4, 2, 0), (80, 0.28, 4, 2, 0), (10, 0.0, 3, 1, 0),
+                                           (9, 0.3, 5, 3, 0), (8, 0.0, 4, 1, 2), (40, 0.14, 4, 2, 2),
+                                           (13, 0.2, 4, 2, 3), (10, 0.0, 3, 1, 1)])
+def test_domains_equal_brute_force_membership(n, obs, b, h, off):
     """Every domain's owned actuators and observed subapertures equal a brute-force membership test
     written per element (distance of the element's grid cell to the block, clipped to the grid),
-    so a dropped or extra halo row or column, at the grid edge or inside, fails."""
+    so a dropped or extra halo row or column, at the grid edge or inside, fails.  Also for block
+    grids shifted by `off` subapertures (the second partition of Sect. 5)."""
     g = geometry.make_geometry(n, obs)
-    doms = geometry.make_domains(g, b, h)
-    nb = -(-n // b)
+    doms = geometry.make_domains(g, b, h, offset=off)
     by_block = {(d.I, d.J): d for d in doms}
     # owned actuators: an actuator (r, c) belongs to the block whose span of subaperture rows and
-    # columns contains it; the corner row/column n lies past the last block and belongs to it
+    # columns, [b I - off, b (I + 1) - off), contains it; the corner row/column n lies past the
+    # last subaperture row and belongs to that row's block
+    def block_of(r):
+        return (min(r, n - 1) + off) // b
     want_owned = {}
     for k, (r, c) in enumerate(g.act_rc):
-        I = nb - 1 if r >= b * (nb - 1) else r // b
-        J = nb - 1 if c >= b * (nb - 1) else c // b
-        want_owned.setdefault((I, J), set()).add(k)
+        want_owned.setdefault((block_of(r), block_of(c)), set()).add(k)
     assert set(by_block) == set(want_owned)          # no block without valid actuators is kept
     for IJ, d in by_block.items():
         assert set(d.owned_act.tolist()) == want_owned[IJ]
@@ -168,8 +171,8 @@ def test_domains_equal_brute_force_membership(n, obs, b, h):
         I, J = IJ
         want = set()
         for k, (r, c) in enumerate(g.sub_rc):
-            gap_r = max(b * I - r, r - (b * (I + 1) - 1), 0)
-            gap_c = max(b * J - c, c - (b * (J + 1) - 1), 0)
+            gap_r = max(b * I - off - r, r - (b * (I + 1) - off - 1), 0)
+            gap_c = max(b * J - off - c, c - (b * (J + 1) - off - 1), 0)
             if gap_r <= h and gap_c <= h:
                 want.add(k)
         assert set(d.obs_sub.tolist()) == want, (IJ, sorted(want ^ set(d.obs_sub.tolist())))

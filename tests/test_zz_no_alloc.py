@@ -65,3 +65,30 @@ def test_static_analysis_rejects_oversized_problem():
     assert _lib.letkf_analyze_static(f.ctx, y.data_ptr(), 0.0, out.data_ptr()) == _lib.LETKF_ESCRATCH
     assert "16 MiB" in _lib.letkf_status_string(_lib.LETKF_ESCRATCH)
     f.close()
+
+
+def test_static_analysis_nonfinite_slope_gives_the_forecast_then_recovers():
+    """A non-finite slope: the output is the context's forecast ensemble bit for bit and
+    LETKF_ENONFINITE is latched; the next finite call equals letkf_analyze again (the call's own
+    reject flag starts from zero every time)."""
+    y, _ = slopes("vlt-40x40", 4)
+    f = gpu_filter("vlt-40x40", "fp32", "plain")
+    dt = f.dtype
+    f.step(torch.as_tensor(y[0], dtype=dt, device="cuda"))
+    before, _ = f.get_state()
+    before = before.clone()
+    bad = torch.as_tensor(y[1], dtype=dt, device="cuda").clone()
+    bad[7] = float("nan")
+    out = torch.full((f.info.n, f.info.m), float("inf"), dtype=dt, device="cuda")
+    assert _lib.letkf_analyze_static(f.ctx, bad.data_ptr(), 0.0, out.data_ptr()) == _lib.LETKF_OK
+    assert torch.equal(out, before)
+    assert f.sync() == _lib.LETKF_ENONFINITE
+    good = torch.as_tensor(y[1], dtype=dt, device="cuda")
+    out.fill_(float("nan"))
+    assert _lib.letkf_analyze_static(f.ctx, good.data_ptr(), 0.0, out.data_ptr()) == _lib.LETKF_OK
+    f.analyze(good)
+    ref, _ = f.get_state()
+    assert torch.isfinite(out).all()
+    assert _rel(out, ref) <= 1e-6, _rel(out, ref)
+    assert f.sync() == 0
+    f.close()
