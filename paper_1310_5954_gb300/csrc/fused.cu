@@ -271,39 +271,50 @@ __device__ __forceinline__ void simt_rows(const SysDesc& A, int e0, int n_own) {
     }
 }
 
-// Thread 0: bulk copies of domain d's halo rows (observed instant) and own rows.
+// Warp 0, all 32 lanes: bulk copies of domain d's halo rows (observed instant) and own rows, lane
+// l issuing rows l, l + 32, ... once lane 0 has announced the bytes on the barrier (one thread
+// issuing them all, with a table read per row, held the CTA ~10 k cycles per domain).
 __device__ __forceinline__ void issue_loads(const SysDesc& A, int d, unsigned char* smem, uint64_t* bar) {
+    const int lane = threadIdx.x & 31;
     float* Xh = reinterpret_cast<float*>(smem + A.off_xh);
     float* XE = reinterpret_cast<float*>(smem + A.off_xe);
     const int e0 = A.tab.own_off[d], n_own = A.tab.own_off[d + 1] - e0;
     const int h0 = A.tab.halo_off[d], n_h = A.tab.halo_off[d + 1] - h0;
     const int n_e = (A.with_forecast && A.a2 == 0.f) ? n_own : 2 * n_own;   // AR(2) needs both instants
     const uint32_t rb = (uint32_t)A.m_pad * 4u;
-    mbar_arrive_expect_tx(bar, rb * (uint32_t)(n_h + n_e));
-    for (int j = 0; j < n_h; ++j)
+    if (lane == 0) mbar_arrive_expect_tx(bar, rb * (uint32_t)(n_h + n_e));
+    __syncwarp();
+    for (int j = lane; j < n_h; j += 32)
         bulk_g2s(Xh + (size_t)j * A.m_pad, A.X + (size_t)(A.row_obs + A.tab.halo[h0 + j]) * A.m_pad, rb, bar);
-    for (int e = 0; e < n_e; ++e) {
+    for (int e = lane; e < n_e; e += 32) {
         const int r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
         bulk_g2s(XE + (size_t)e * A.m_pad, A.X + (size_t)r * A.m_pad, rb, bar);
     }
 }
 
-// Thread 0: take the next work item of the batch.  Its loads are issued at once when they
-// cannot overwrite shared memory still in use (everything at or above busy_from).
+// Warp 0, all 32 lanes: take the next work item of the batch.  Its loads are issued at once when
+// they cannot overwrite shared memory still in use (everything at or above busy_from).
 __device__ void fetch_item(const FusedBatch& B, Ctrl* ctl, unsigned char* smem, int busy_from) {
-    const int g = atomicAdd(B.queue, 1);
-    ctl->item = g;
-    ctl->loaded = 0;
+    const int lane = threadIdx.x & 31;
+    int g = 0;
+    if (lane == 0) g = atomicAdd(B.queue, 1);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (lane == 0) {
+        ctl->item = g;
+        ctl->loaded = 0;
+    }
     if (g >= B.n_items) return;
     int s = 0;
     while (s + 1 < B.n_sys && g >= B.sys[s + 1].item0) ++s;
     const SysDesc& A = B.sys[s];
     const int d = A.tab.order[g - A.item0];
-    ctl->sys = s;
-    ctl->dom = d;
+    if (lane == 0) {
+        ctl->sys = s;
+        ctl->dom = d;
+    }
     if (!A.dual && A.tab.obs_off[d + 1] > A.tab.obs_off[d] && A.off_big <= busy_from) {
         issue_loads(A, d, smem, &ctl->bar_load);
-        ctl->loaded = 1;
+        if (lane == 0) ctl->loaded = 1;
     }
 }
 
@@ -1189,7 +1200,7 @@ __device__ __noinline__ const float* analyse_simt(const FusedBatch& B, Ctrl* ctl
         E[e * lm + i] = XE[(size_t)e * A.m_pad + i] - xe_mean[e];
     }
     __syncthreads();
-    if (tid == 0) fetch_item(B, ctl, smem, A.off_big);
+    if ((tid >> 5) == 0) fetch_item(B, ctl, smem, A.off_big);
     // ---- transform
     const float rs = rsqrtf(s_ns);    // T = Z / sqrt(s_ns) (m x m form); Z / sqrt(s_ns) = (I + K/c)^(-1/2)
     *ld_out = lm;
@@ -1258,7 +1269,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
     // read what this kernel writes)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
+    if (warp == 0) fetch_item(B, ctl, smem, 1 << 30);
     __syncthreads();
 
     while (ctl->item < B.n_items && !ctl->abort) {
@@ -1312,11 +1323,11 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         if (n_obs == 0) {
             simt_rows(A, e0, n_own);
             __syncthreads();
-            if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
+            if (warp == 0) fetch_item(B, ctl, smem, 1 << 30);
             __syncthreads();
             continue;
         }
-        if (tid == 0 && !A.dual && !ctl->loaded) issue_loads(A, d, smem, &ctl->bar_load);
+        if (warp == 0 && !A.dual && !ctl->loaded) issue_loads(A, d, smem, &ctl->bar_load);
         // ---- frame ingest: a non-finite slope in this domain's observation region rejects the
         //      system's frame (its state is restored when the launch ends)
         int nonfinite = 0;
@@ -1335,7 +1346,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 break;
             }
             __syncthreads();
-            if (tid == 0) fetch_item(B, ctl, smem, 1 << 30);
+            if (warp == 0) fetch_item(B, ctl, smem, 1 << 30);
             __syncthreads();
             continue;
         }
@@ -1346,21 +1357,45 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             if (tid == 0) {
                 atomicExch(A.dom_bad, 1);
                 atomicOr(A.status, ST_NONFINITE);
-                fetch_item(B, ctl, smem, 1 << 30);
             }
+            if (warp == 0) fetch_item(B, ctl, smem, 1 << 30);
             __syncthreads();
             continue;
         }
         // ---- 2. halo anomalies; slopes (x and y of each subaperture interleaved along K:
         //        k = 2 s + direction) and the innovation row as the Gram operand
-        for (int j = warp; j < n_h; j += FT / 32) {
-            float sm_ = 0.f;
-            for (int i = lane; i < m; i += 32) sm_ += Xh[(size_t)j * A.m_pad + i];
-            sm_ = warp_sum(sm_);
-            const float mu = sm_ / (float)m;
-            for (int i = lane; i < m; i += 32) Xh[(size_t)j * A.m_pad + i] -= mu;
-            if (lane == 0) xh_mean[j] = mu;
+        // two rows per warp at a time, the values kept in registers between the sum and the
+        // subtraction (m <= 127 here: four values per lane and row)
+        for (int j0 = warp; j0 < n_h; j0 += 2 * (FT / 32)) {
+            const int j1 = j0 + FT / 32;
+            float v0[4], v1[4], s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = lane + 32 * u;
+                v0[u] = i < m ? Xh[(size_t)j0 * A.m_pad + i] : 0.f;
+                v1[u] = (i < m && j1 < n_h) ? Xh[(size_t)j1 * A.m_pad + i] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s0 += v0[u];
+                s1 += v1[u];
+            }
+            s0 = warp_sum(s0);
+            s1 = warp_sum(s1);
+            const float mu0 = s0 / (float)m, mu1 = s1 / (float)m;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = lane + 32 * u;
+                if (i < m) Xh[(size_t)j0 * A.m_pad + i] = v0[u] - mu0;
+                if (i < m && j1 < n_h) Xh[(size_t)j1 * A.m_pad + i] = v1[u] - mu1;
+            }
+            if (lane == 0) {
+                xh_mean[j0] = mu0;
+                if (j1 < n_h) xh_mean[j1] = mu1;
+            }
         }
+        int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
+        for (int t = tid; t < n_obs; t += FT) pcs[t] = A.tab.obs_corner[o0 + t];
         __syncthreads();
         // ---- small domains: the FP32 SIMT analysis leaves X'_E T in shared memory
         const bool simt = A.simt_q > 0 && min(p_loc, m) <= A.simt_q;
@@ -1377,7 +1412,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     const int sidx = 4 * kc + u;
                     float sx = 0.f, sy = 0.f;
                     if (i <= m && sidx < n_obs) {
-                        const int pc = A.tab.obs_corner[o0 + sidx];
+                        const int pc = pcs[sidx];
                         const int c00 = pc & 0xFF, c01 = (pc >> 8) & 0xFF, c10 = (pc >> 16) & 0xFF, c11 = (pc >> 24) & 0xFF;
                         float a00, a01, a10, a11;
                         if (i < m) {
@@ -1644,8 +1679,6 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             // h = X'_h w_bar and S^T t is X'_h^T applied to the stencil's transpose of t: n_h x m
             // products instead of rebuilding every slope from its four corners
             float* hv = vec + 1536;                  // 256: halo-actuator vector
-            int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
-            for (int s = tid; s < n_obs; s += FT) pcs[s] = A.tab.obs_corner[o0 + s];
             const int n_ref = s_scale > A.s_split ? 2 : 1;
             for (int ref = 0; ref < n_ref; ++ref) {
                 for (int j = warp; j < n_h; j += FT / 32) {        // h = X'_h w_bar
@@ -1732,9 +1765,9 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 tc_fence_after();
                 issue_product(tbase + TM_P, Ah, Al, Bh, Bl, NP, NP, A.tr_terms, 1);   // X'_E T
                 mma_commit(&ctl->bar_mma);
-                // the halo and own-row tiles are free now: fetch the next domain's under this product
-                fetch_item(B, ctl, smem, A.off_big);
             }
+            // the halo and own-row tiles are free now: fetch the next domain's under this product
+            if (warp == 0) fetch_item(B, ctl, smem, A.off_big);
             if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
             ph_mma ^= 1;
             tc_fence_after();
@@ -1789,9 +1822,16 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             __syncthreads();
         }
         const bool writes = mine && !(ar2 && row >= n_own);
+        const bool dense_v = writes && A.with_forecast && A.vmode == 0;
         float psum = 0.f;
 #pragma unroll 1
         for (int q8 = 0; q8 < nq; ++q8) {
+            float vq[8];     // this chunk's process noise, loaded before the tensor-memory read
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = col0 + 8 * q8 + u;
+                vq[u] = (dense_v && j < m) ? A.V[(size_t)jact * A.m_pad + j] : 0.f;
+            }
             float dv[8];
             prow(q8, dv);
             if (!writes) continue;
@@ -1803,7 +1843,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     if (A.with_forecast) {
                         float v = 0.f;
                         if (A.vmode == 0) {
-                            v = A.V[(size_t)jact * A.m_pad + j];
+                            v = vq[u];
                         } else if (A.vmode == 1) {
                             float zz[4];
                             normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);

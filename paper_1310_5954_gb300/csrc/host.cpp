@@ -247,6 +247,8 @@ void free_all(letkf_ctx* c) {
     }
     if (c->Xi_side) cudaFree(c->Xi_side);
     if (c->pair_pred) cudaFree(c->pair_pred);
+    for (void* q : {c->rg_items, c->rg_tiles, static_cast<void*>(c->rg_count), c->rg_part})
+        if (q) cudaFree(q);
     if (c->scratch) cudaFree(c->scratch);
     letkf::fused_graph_reset(c);
     letkf::global_free(c);
@@ -316,6 +318,8 @@ size_t footprint_bytes(const letkf_params* p, const HostModel& h) {
         b += letkf::noise_xi_bytes(h.n_act, p->m);
     } else if (p->q_sqrt) {
         b += na * na * eb + na * row;
+        if (p->path != LETKF_PATH_GLOBAL)
+            b += letkf::rg_bytes(h.n_act, p->m, letkf::lower_triangular(p->q_sqrt, h.n_act), eb);
     }
     if (p->piston != LETKF_PISTON_OFF) b += letkf::piston_bytes(h, (int)nd, (int)eb);
     if (p->path == LETKF_PATH_GLOBAL) {

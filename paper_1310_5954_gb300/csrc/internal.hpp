@@ -134,6 +134,13 @@ struct letkf_ctx {
     int cap_dom = -1;
     // fused path: this context's prediction when it is the second filter of letkf_step_pair
     void* pair_pred = nullptr;
+    // FP32 / FP64 dense process noise: work items and tiles (int4), per-tile counters and partial
+    // tiles of the split-K draw V = L xi
+    void* rg_items = nullptr;
+    void* rg_tiles = nullptr;
+    int* rg_count = nullptr;
+    void* rg_part = nullptr;
+    int rg_n_items = 0;
     // stage timing
     int prof_on = 0;
     std::vector<int> prof_stage;            // stage of each record
@@ -163,6 +170,14 @@ int draw_perturbations(letkf_ctx* c, unsigned long long frame);
 // Normals of `frame` into xi, then V = L xi into v_out, on `stream`.
 int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream);
 int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host);
+// Split-K work plan of the per-frame draw V = L xi (n x n factor, m members): items and tiles
+// (4 ints each, filled when not null), partial-tile slots; rg_bytes: its device bytes.
+struct RowGemmPlan {
+    int n_items = 0, n_tiles = 0, n_slots = 0;
+    size_t part_elems = 0;
+};
+RowGemmPlan rg_plan(int n, int m, bool lower, int* items, int* tiles);
+size_t rg_bytes(int n, int m, bool lower, size_t eb);
 // Node parameters of the normals kernel draw_perturbations_on launches (arguments held in *nn).
 struct NormalsNode {
     cudaKernelNodeParams params;

@@ -207,8 +207,113 @@ __global__ void __launch_bounds__(RG_THREADS) row_gemm_kernel(const T* __restric
     }
 }
 
+// The per-frame draw V = L Xi with split K: a work item is a 64 x 128 tile of V over one piece of
+// at most RK_KC values of k (with a lower-triangular L, a row block's k stops at its last row), so
+// that the long row blocks of a triangular factor spread over many CTAs.  256 threads, each a
+// 4 x 8 register block (rows ty + 16 i, columns tx + 16 j), K steps of 16 staged in shared memory
+// with a register prefetch.  A tile of one piece writes V; otherwise each piece writes its partial
+// tile to the scratch and the CTA that finishes last (per-tile counter) sums the pieces in piece
+// order, so the result does not depend on which CTA ran first, and resets the counter.
+constexpr int RK_BM = 64, RK_BN = 128, RK_BK = 16, RK_KC = 512, RK_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(RK_THREADS) rg_splitk_kernel(const T* __restrict__ L, const T* __restrict__ Xi,
+                                                               T* __restrict__ V, int n, int m, int ldx, int ldv,
+                                                               const int4* __restrict__ items,
+                                                               const int4* __restrict__ tiles, T* __restrict__ part,
+                                                               int* __restrict__ count) {
+    __shared__ T As[RK_BK][RK_BM + 1];   // As[k][row]: L tile, transposed
+    __shared__ T Bs[RK_BK][RK_BN];       // Bs[k][col]: Xi tile
+    __shared__ int last;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int4 it = items[blockIdx.x];   // tile, k0, k1, piece
+    const int4 tl = tiles[it.x];         // row block, column block, pieces, first scratch slot
+    const int r0 = tl.x * RK_BM, c0 = tl.y * RK_BN, k0 = it.y, k1 = it.z;
+    // loads: A, 64 rows x 16 k, thread -> row tid / 4, k 4 (tid % 4) .. + 3;
+    //        B, 16 k x 128 columns, thread -> k tid / 16, columns 8 (tid % 16) .. + 7
+    const int ar = tid >> 2, ak = 4 * (tid & 3);
+    const int bk = tid >> 4, bc = 8 * (tid & 15);
+    T ra[4], rb[8];
+    auto fetch = [&](int kb) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + ar, k = kb + ak + u;
+            ra[u] = (r < n && k < k1) ? L[(size_t)r * n + k] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = kb + bk, cc = c0 + bc + u;
+            rb[u] = (k < k1 && cc < m) ? Xi[(size_t)k * ldx + cc] : T(0);
+        }
+    };
+    T acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+    if (k0 < k1) fetch(k0);
+    for (int kb = k0; kb < k1; kb += RK_BK) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) As[ak + u][ar] = ra[u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) Bs[bk][bc + u] = rb[u];
+        __syncthreads();
+        if (kb + RK_BK < k1) fetch(kb + RK_BK);
+#pragma unroll
+        for (int k = 0; k < RK_BK; ++k) {
+            T a[4], b[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    if (tl.z == 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = r0 + ty + 16 * i;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int cc = c0 + tx + 16 * j;
+                if (r < n && cc < m) V[(size_t)r * ldv + cc] = acc[i][j];
+            }
+        }
+        return;
+    }
+    T* mine = part + (size_t)(tl.w + it.w) * RK_BM * RK_BN;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine[(ty + 16 * i) * RK_BN + tx + 16 * j] = acc[i][j];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&count[it.x], 1) == tl.z - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int cc = c0 + tx + 16 * j;
+            const size_t off = (size_t)(ty + 16 * i) * RK_BN + tx + 16 * j;
+            T s = T(0);
+            for (int p = 0; p < tl.z; ++p) s += part[(size_t)(tl.w + p) * RK_BM * RK_BN + off];
+            if (r < n && cc < m) V[(size_t)r * ldv + cc] = s;
+        }
+    }
+    if (tid == 0) count[it.x] = 0;
+}
+
 // FP64 / FP32: V (n_act x m, ld m_pad) = L (n_act x n_act, row-major) * Xi (n_act x m, ld xld) on
-// `stream`.  (Mixed precision uses noise.cu.)
+// `stream`.  (Mixed precision uses noise.cu.)  The per-frame draw uses the split-K kernel and the
+// context's work tables; the initial ensemble's products (once) the plain row_gemm_kernel.
 int noise_gemm(letkf_ctx* c, const void* L, const void* Xi, int xld, int gemm_type, void* V, cudaStream_t stream,
                bool lower) {
     const int m = c->m, na = c->n_act;
@@ -255,6 +360,23 @@ int draw_perturbations_impl(letkf_ctx* c, unsigned long long frame) {
     return draw_perturbations_on(c, frame, c->Xi, c->V, c->stream);
 }
 
+// The per-frame product with the split-K kernel (work tables made by rg_prepare).
+int noise_gemm_split(letkf_ctx* c, const void* Xi, int gemm_type, void* V, cudaStream_t stream) {
+    if (c->rg_n_items < 1) return LETKF_EINVAL;
+    const int m = c->m, na = c->n_act;
+    if (gemm_type == 0)
+        rg_splitk_kernel<double><<<c->rg_n_items, RK_THREADS, 0, stream>>>(
+            (const double*)c->Lq, (const double*)Xi, (double*)V, na, m, c->m_pad, c->m_pad, (const int4*)c->rg_items,
+            (const int4*)c->rg_tiles, (double*)c->rg_part, c->rg_count);
+    else if (gemm_type == 1)
+        rg_splitk_kernel<float><<<c->rg_n_items, RK_THREADS, 0, stream>>>(
+            (const float*)c->Lq, (const float*)Xi, (float*)V, na, m, c->m_pad, c->m_pad, (const int4*)c->rg_items,
+            (const int4*)c->rg_tiles, (float*)c->rg_part, c->rg_count);
+    else
+        return LETKF_EINVAL;
+    return cudaGetLastError() == cudaSuccess ? LETKF_OK : LETKF_ECUDA;
+}
+
 int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void* v_out, cudaStream_t stream) {
     if (c->Lt) return noise_draw(c, frame, xi, v_out, stream);
     const int gt = gemm_type_of(c);
@@ -267,12 +389,12 @@ int draw_perturbations_on(letkf_ctx* c, unsigned long long frame, void* xi, void
         normals_kernel<float><<<g, 256, 0, stream>>>((float*)xi, c->m_pad, c->n_act, c->m, c->seed, 1u,
                                                      (uint32_t)frame);
     if (cudaGetLastError() != cudaSuccess) return LETKF_ECUDA;
-    return noise_gemm(c, c->Lq, xi, c->m_pad, gt, v_out, stream, c->lq_lower != 0);
+    return noise_gemm_split(c, xi, gt, v_out, stream);
 }
 
 int draw_product_on(letkf_ctx* c, const void* xi, void* v_out, cudaStream_t stream) {
     if (c->Lt) return noise_product(c, xi, v_out, stream);
-    return noise_gemm(c, c->Lq, xi, c->m_pad, gemm_type_of(c), v_out, stream, c->lq_lower != 0);
+    return noise_gemm_split(c, xi, gemm_type_of(c), v_out, stream);
 }
 
 // Kernel-node parameters of the normals launch draw_perturbations_on makes for `frame` into xi
@@ -343,6 +465,55 @@ int launch_forecast(letkf_ctx* c, const void* v_user, void* xpred, int in_analys
 // Initial ensemble (Sect. 2.2): second instant = P0 xi0, first = a * second + L xi1, with
 // xi0, xi1 the Philox draws (stream 0, frames 0 and 1).  P0 defaults to L times the stationary
 // standard deviation of the AR model (1 / sqrt(1 - a^2) for AR(1)).
+RowGemmPlan rg_plan(int n, int m, bool lower, int* items, int* tiles) {
+    RowGemmPlan P;
+    const int nrb = (n + RK_BM - 1) / RK_BM, ncb = (m + RK_BN - 1) / RK_BN;
+    for (int rb = 0; rb < nrb; ++rb)
+        for (int cb = 0; cb < ncb; ++cb) {
+            const int kend = lower ? std::min(n, (rb + 1) * RK_BM) : n;
+            const int np = std::max(1, (kend + RK_KC - 1) / RK_KC);
+            if (tiles) {
+                int* t = tiles + 4 * P.n_tiles;
+                t[0] = rb; t[1] = cb; t[2] = np; t[3] = np > 1 ? P.n_slots : 0;
+            }
+            for (int p = 0; p < np; ++p) {
+                if (items) {
+                    int* it = items + 4 * P.n_items;
+                    it[0] = P.n_tiles; it[1] = p * RK_KC; it[2] = std::min(kend, (p + 1) * RK_KC); it[3] = p;
+                }
+                ++P.n_items;
+            }
+            if (np > 1) P.n_slots += np;
+            ++P.n_tiles;
+        }
+    P.part_elems = (size_t)P.n_slots * RK_BM * RK_BN;
+    return P;
+}
+
+size_t rg_bytes(int n, int m, bool lower, size_t eb) {
+    const RowGemmPlan P = rg_plan(n, m, lower, nullptr, nullptr);
+    return 16 * (size_t)P.n_items + 16 * (size_t)P.n_tiles + 4 * (size_t)P.n_tiles + eb * P.part_elems;
+}
+
+// Work tables, counters and scratch of the per-frame split-K draw.
+int rg_prepare(letkf_ctx* c, size_t eb) {
+    const RowGemmPlan P = rg_plan(c->n_act, c->m, c->lq_lower != 0, nullptr, nullptr);
+    std::vector<int> items(4 * (size_t)P.n_items), tiles(4 * (size_t)P.n_tiles);
+    rg_plan(c->n_act, c->m, c->lq_lower != 0, items.data(), tiles.data());
+    if (cudaMalloc(&c->rg_items, items.size() * 4) != cudaSuccess ||
+        cudaMalloc(&c->rg_tiles, tiles.size() * 4) != cudaSuccess ||
+        cudaMalloc((void**)&c->rg_count, (size_t)P.n_tiles * 4) != cudaSuccess)
+        return LETKF_ENOMEM;
+    if (P.part_elems && cudaMalloc(&c->rg_part, P.part_elems * eb) != cudaSuccess) return LETKF_ENOMEM;
+    if (cudaMemcpy(c->rg_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->rg_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->rg_count, 0, (size_t)P.n_tiles * 4) != cudaSuccess)
+        return LETKF_ECUDA;
+    c->rg_n_items = P.n_items;
+    c->device_bytes += rg_bytes(c->n_act, c->m, c->lq_lower != 0, eb);
+    return LETKF_OK;
+}
+
 int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
     const int na = c->n_act, m = c->m;
     const bool f64 = c->precision == LETKF_PREC_FP64;
@@ -375,6 +546,10 @@ int init_ensemble(letkf_ctx* c, const double* L_host, const double* P0_host) {
         if (cudaMalloc(&c->Xi, xib) != cudaSuccess) return LETKF_ENOMEM;
         cudaMemset(c->Xi, 0, xib);
         c->device_bytes += xib;
+        if (c->path != LETKF_PATH_GLOBAL) {   // the global path draws with its tiled GEMM
+            const int rc = rg_prepare(c, eb);
+            if (rc) return rc;
+        }
     }
     // the initial ensemble itself is formed at full state precision (FP64 or FP32 GEMMs)
     const int gt = f64 ? 0 : 1;
