@@ -70,7 +70,8 @@ typedef enum letkf_precision {
     LETKF_PREC_MIXED = 2    /* fused path only: BF16 tensor-core products with FP32 accumulation
                                (single-BF16 Gram, split-BF16 Newton-Schulz and transform), mean
                                weights refined in FP32 against the exact slopes, mean updates
-                               summed in FP64; small domains (simt_q_max) in FP32 on the CUDA cores */
+                               summed in compensated FP32 (twice the working precision); small
+                               domains (simt_q_max) in FP32 on the CUDA cores */
 } letkf_precision;
 
 typedef enum letkf_path {

@@ -14,12 +14,13 @@
 //      (matrix inverse square root by matrix products only; operands split into BF16
 //      high and low parts, three products per step, which holds FP32-level accuracy);
 //   4. mean weights w_bar = [(m-1)I + G]^-1 b = Z (Z b) / ((m-1) s), refined once with the
-//      residual b - ((m-1)I + G) w_bar summed in FP64;
+//      residual against the exact FP32 slopes;
 //   5. X_a[E] = x_bar[E] 1^T + X'[E] (T + w_bar 1^T) as one more MMA, whose epilogue applies
 //      the AR(1) forecast (first instant <- a x_a + v, second <- x_a) and writes x_hat(k+1|k).
 //
-// Precision LETKF_PREC_MIXED uses single BF16 operands for the Gram and the transform;
-// LETKF_PREC_FP32 uses the three-product split everywhere.
+// Precision LETKF_PREC_MIXED uses single BF16 operands for the Gram while its conditioning bound
+// s is at most s_split (8), the three-product split otherwise and for the Newton-Schulz and
+// transform products; LETKF_PREC_FP32 uses the three-product split everywhere.
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -87,6 +88,7 @@ struct SysDesc {
     // shared-memory layout (bytes from the dynamic base); vec and XE start at the same offset
     // for every system, so a region below off_big never overlaps another system's operands
     int off_vec, off_xe, off_xh, off_big, sz_op, sz_opg, sz_a;
+    int off_zf;          // m x m form: FP32 rows of Z in the big region, past the transform's operands
     // test instrument: when cap is set, the analysis of domain cap_dom writes what it computed
     // (header, mean weights, transform or its factors; layout in letkf_set_capture) to cap
     float* cap;
@@ -127,7 +129,6 @@ struct Ctrl {
     float s;
     float rn;
     float red[FT / 32];
-    double redd[FT / 32];
     SysDesc sd;          // the current item's system (copied from the kernel parameters)
 };
 static_assert(sizeof(Ctrl) <= 1024, "control block overlaps the vector area");
@@ -232,6 +233,93 @@ __device__ __forceinline__ float block_sum(Ctrl* ctl, float v) {
 #pragma unroll
     for (int w = 0; w < FT / 32; ++w) s += ctl->red[w];
     __syncthreads();
+    return s;
+}
+
+// This thread's half-row of a tensor-memory matrix (from taddr, nq chunks of 8 columns) passed to
+// f(q8, v) chunk by chunk, the next chunk's load in flight while f runs.  f must issue no tensor-
+// memory load of its own.
+template <typename F>
+__device__ __forceinline__ void tmem_rows(uint32_t taddr, int nq, F&& f) {
+    uint32_t rc[8], rn[8];
+    tmem_ld8_async(taddr, rc);
+    tmem_wait_ld(rc);
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {
+        if (q8 + 1 < nq) tmem_ld8_async(taddr + 8 * (q8 + 1), rn);
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __uint_as_float(rc[u]);
+        f(q8, v);
+        if (q8 + 1 < nq) {
+            tmem_wait_ld(rn);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) rc[u] = rn[u];
+        }
+    }
+}
+
+// 8 consecutive floats of a row in global memory, of which the first `valid` exist (16-byte aligned
+// at dst): two 16-byte accesses when all 8 do, else element by element.  A warp's threads write
+// different rows, so vector accesses cut the number of scattered sectors by four.
+__device__ __forceinline__ void put8(float* dst, const float (&v)[8], int valid) {
+    if (valid >= 8) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (u < valid) dst[u] = v[u];
+    }
+}
+__device__ __forceinline__ void get8(const float* src, float (&v)[8], int valid) {
+    if (valid >= 8) {
+        const float4 a = reinterpret_cast<const float4*>(src)[0], b = reinterpret_cast<const float4*>(src)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = u < valid ? src[u] : 0.f;
+    }
+}
+
+// Compensated sum of products in FP32 (the dot product Dot2 of Ogita, Rump and Oishi, SIAM J. Sci.
+// Comput. 26, 2005): each product is split exactly into p + pe by an FMA, each partial sum into
+// t + e by TwoSum, and the error terms are summed alongside, so the result is as accurate as a sum
+// in twice the working precision.  It replaces FP64 sums, which GB300's FP64 pipe makes slow.
+// Explicit _rn operations keep the compiler from fusing the error-free transformations.
+__device__ __forceinline__ void dot2_add(float& s, float& c, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
+// Warp reduction of the (s, c) pairs of dot2_add; lane 0's result is the one used.
+__device__ __forceinline__ float dot2_warp(float s, float c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        const float t = __fadd_rn(s, s2);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(c2, e));
+    }
+    return __fadd_rn(s, c);
+}
+
+// block_sum without its closing barrier: the caller passes a CTA barrier before the next block-wide
+// reduction reuses ctl->red.
+__device__ __forceinline__ float block_sum_open(Ctrl* ctl, float v) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) ctl->red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < FT / 32; ++w) s += ctl->red[w];
     return s;
 }
 
@@ -544,6 +632,16 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         rn_prev = rn;
         if (conv) break;
         to_mma();
+        if (rn < ns_last) {    // the last update (see the m x m form): only T Z is used afterwards
+            if (tid == 0) {
+                tc_fence_after();
+                issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
+                mma_commit(&ctl->bar_mma);
+            }
+            if (!mma_wait()) return false;
+            z_in_tmem = true;
+            break;
+        }
         if (tid == 0) {
             tc_fence_after();
             issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
@@ -563,7 +661,6 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
         z_in_tmem = true;
         to_mma();
-        if (rn < ns_last) break;       // as in the m x m form: the last update lands at the floor
     }
     if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
     tc_fence_before();
@@ -743,7 +840,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         issue_product(tbase + TM_Y, Zt_h, Zt_l, Wh, Wl, NP, MP, 3, 1);    // W = (Z / sqrt(c)) S
         mma_commit(&ctl->bar_mma);
     }
-    // own rows: member mean and the mean update X'_E w_bar (FP64 sums), under the product
+    // own rows: member mean and the mean update X'_E w_bar (compensated sums), under the product
     for (int e = warp; e < n_e; e += FT / 32) {
         const int r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
         const float* x = A.X + (size_t)r * A.m_pad;
@@ -751,13 +848,12 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         for (int i = lane; i < m; i += 32) sm_ += x[i];
         sm_ = warp_sum(sm_);
         const float mu = sm_ / (float)m;
-        double u = 0.0;
-        for (int i = lane; i < m; i += 32) u += (double)(x[i] - mu) * (double)wbar[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        float us = 0.f, uc = 0.f;
+        for (int i = lane; i < m; i += 32) dot2_add(us, uc, x[i] - mu, wbar[i]);
+        const float u = dot2_warp(us, uc);
         if (lane == 0) {
             xe_mean[e] = mu;
-            uvec[e] = (float)u;
+            uvec[e] = u;
         }
     }
     if (!mma_wait()) return false;
@@ -1007,7 +1103,7 @@ __device__ void simt_mv(float* y, const float* A, int ar, int ac, const float* x
     __syncthreads();
 }
 
-// Member mean of each analysed own row and its mean update X'_E w_bar (FP64 sums).
+// Member mean of each analysed own row and its mean update X'_E w_bar (compensated sums, dot2_add).
 __device__ __forceinline__ void own_row_means(const SysDesc& A, const float* XE, int n_e, const float* wbar,
                                               float* xe_mean, float* uvec) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, m = A.m;
@@ -1016,13 +1112,12 @@ __device__ __forceinline__ void own_row_means(const SysDesc& A, const float* XE,
         for (int i = lane; i < m; i += 32) sm_ += XE[(size_t)e * A.m_pad + i];
         sm_ = warp_sum(sm_);
         const float mu = sm_ / (float)m;
-        double u = 0.0;
-        for (int i = lane; i < m; i += 32) u += (double)(XE[(size_t)e * A.m_pad + i] - mu) * (double)wbar[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        float us = 0.f, uc = 0.f;
+        for (int i = lane; i < m; i += 32) dot2_add(us, uc, XE[(size_t)e * A.m_pad + i] - mu, wbar[i]);
+        const float u = dot2_warp(us, uc);
         if (lane == 0) {
             xe_mean[e] = mu;
-            uvec[e] = (float)u;
+            uvec[e] = u;
         }
     }
     __syncthreads();
@@ -1395,6 +1490,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             }
         }
         int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
+        uchar4* inc4 = reinterpret_cast<uchar4*>(xh_mean);   // over the halo means once they are used
         for (int t = tid; t < n_obs; t += FT) pcs[t] = A.tab.obs_corner[o0 + t];
         __syncthreads();
         // ---- small domains: the FP32 SIMT analysis leaves X'_E T in shared memory
@@ -1441,10 +1537,24 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             }
             fence_async_smem();
             __syncthreads();
+            // the incidence of the halo actuators in the observed subapertures, for the refinement's
+            // S^T products, over the halo means (no longer read): inc4[j].{x,y,z,w} = the
+            // subaperture whose corner 00, 01, 10, 11 is halo actuator j (0xFF: none).  Cleared
+            // here, filled under the Gram product (each subaperture writes its own four slots)
+            for (int j = tid; j < n_h; j += FT) inc4[j] = make_uchar4(0xFF, 0xFF, 0xFF, 0xFF);
+            __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
                 issue_product(tbase + TM_G, opg_h, opg_l, opg_h, opg_l, KP, NP, A.gram_terms, 0);
                 mma_commit(&ctl->bar_mma);
+            }
+            for (int s2 = tid; s2 < n_obs; s2 += FT) {
+                unsigned char* inc = reinterpret_cast<unsigned char*>(inc4);
+                const int pc = pcs[s2];
+                inc[4 * (pc & 0xFF) + 0] = (unsigned char)s2;
+                inc[4 * ((pc >> 8) & 0xFF) + 1] = (unsigned char)s2;
+                inc[4 * ((pc >> 16) & 0xFF) + 2] = (unsigned char)s2;
+                inc[4 * ((pc >> 24) & 0xFF) + 3] = (unsigned char)s2;
             }
             if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
             ph_mma ^= 1;
@@ -1452,17 +1562,14 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             // ---- 3a. G and b; scale s = 1 + ||G||_F / c, an upper bound of cond((m-1)I + G)
             auto read_gram = [&]() -> float {
                 float fr = 0.f;
-    #pragma unroll 1
-                for (int q8 = 0; q8 < nq; ++q8) {
-                    float g[8];
-                    tmem_ld8(tl + TM_G + 8 * q8, g);
+                tmem_rows(tl + TM_G, nq, [&](int q8, const float (&g)[8]) {
     #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int j = col0 + 8 * q8 + u;
                         if (row < m && j < m) fr += g[u] * g[u];
                         if (row < m && j == m) bvec[row] = g[u];
                     }
-                }
+                });
                 return block_sum(ctl, fr);
             };
             float fro = read_gram();
@@ -1486,17 +1593,17 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             const float ns_last = ns_stop(A.ns_last, A.gram_terms, s_scale, A.s_split);
             // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
             //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
-            //      Z_1 = T_0: one pass over G writes Y_0, T_0 (also as Z_1) and the residual.
+            //      Z_1 = T_0: one pass over G writes Y_0, T_0 as Z_1 and the residual; Y_1 = Y_0 T_0
+            //      reads T_0 from Z's buffer (T_0 is symmetric: its K-major and MN-major operand
+            //      layouts hold the same bytes).
             int z_state = 1;     // where Z is: 0 identity, 1 shared memory only (Z_1 = T_0), 2 also TMEM
             int it = 1;
             bool ok = true;
             float rn_prev;
             {
                 float r2 = 0.f;
-    #pragma unroll 1
-                for (int q8 = 0; q8 < nq; ++q8) {
-                    float g[8], yv[8], tv[8];
-                    tmem_ld8(tl + TM_G + 8 * q8, g);
+                tmem_rows(tl + TM_G, nq, [&](int q8, const float (&g)[8]) {
+                    float yv[8], tv[8];
     #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int j = col0 + 8 * q8 + u;
@@ -1509,11 +1616,10 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     }
                     if (row < NP) {
                         store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                        store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
                         store8(Zh, Zl, row, col0 + 8 * q8, NP, tv, true);
                     }
-                }
-                rn_prev = sqrtf(block_sum(ctl, r2));
+                });
+                rn_prev = sqrtf(block_sum_open(ctl, r2));   // a barrier follows on either branch
             }
             if (rn_prev < 2e-6f * (float)m) {
                 z_state = 0;     // converged at once: Z = I
@@ -1524,18 +1630,15 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 __syncthreads();
                 if (tid == 0) {
                     tc_fence_after();
-                    issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
+                    issue_product(tbase + TM_Y, Yh, Yl, Zh, Zl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
                     mma_commit(&ctl->bar_mma);
                 }
                 if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) break;
                 ph_mma ^= 1;
                 tc_fence_after();
-    #pragma unroll 1
-                for (int q8 = 0; q8 < nq; ++q8) {
-                    float yv[8];
-                    tmem_ld8(tl + TM_Y + 8 * q8, yv);
+                tmem_rows(tl + TM_Y, nq, [&](int q8, const float (&yv)[8]) {
                     if (row < NP) store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                }
+                });
                 fence_async_smem();
                 tc_fence_before();
                 __syncthreads();
@@ -1577,14 +1680,35 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                         }
                     }
                 }
-                r2 = block_sum(ctl, r2);
+                // one barrier for the residual's block sum and T's stores (to the tensor core)
+                r2 = warp_sum(r2);
+                if (lane == 0) ctl->red[warp] = r2;
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                r2 = 0.f;
+    #pragma unroll
+                for (int w = 0; w < FT / 32; ++w) r2 += ctl->red[w];
                 const float rn = sqrtf(r2);
                 const bool conv = rn < 2e-6f * (float)m || (rn < 2e-2f && rn > 0.6f * rn_prev);
                 rn_prev = rn;
                 if (conv) break;
-                fence_async_smem();
-                tc_fence_before();
-                __syncthreads();
+                // the update after which ||I - P|| lands at the rounding floor is the last: only its
+                // T Z is used afterwards (read from tensor memory), so Y T and the operand stores
+                // are skipped
+                const bool last = rn < ns_last;
+                if (last) {
+                    if (tid == 32) {
+                        tc_fence_after();
+                        issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
+                        mma_commit(&ctl->bar_mma2);
+                    }
+                    if (!wait_all(ctl, &ctl->bar_mma2, ph_mma2, A.status)) { ok = false; break; }
+                    ph_mma2 ^= 1;
+                    tc_fence_after();
+                    z_state = 2;
+                    break;
+                }
                 // the two products are issued by threads of different warps, so their issue loops
                 // (one tcgen05.mma per K step and BF16 term) overlap
                 if (tid == 0) {
@@ -1621,9 +1745,6 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 fence_async_smem();
                 tc_fence_before();
                 __syncthreads();
-                // the update just applied takes ||I - P|| to ~0.75 ||I - P||^2, under the rounding of
-                // the result once ||I - P|| < ns_last: the product that would confirm it is skipped
-                if (rn < ns_last) break;
             }
             if (!ok) break;
             if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
@@ -1652,16 +1773,44 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     for (int u = 0; u < 8; ++u) zv[u] = (row == col0 + 8 * q8 + u && row < m) ? 1.f : 0.f;
                 }
             };
-            // y_out[row] = sum_j Z[row][j] x_in[j]  (all rows; rows >= m give 0)
-            auto zmatvec = [&](const float* x_in, float* y_out) {
-                float part = 0.f;
+            // Z as FP32 rows in shared memory (row stride NP + 4: conflict-free 16-byte reads down a
+            // column of threads), zero outside m x m; the mean weights' matrix-vector products and
+            // the transform's operand read it there instead of tensor memory
+            float* zf = reinterpret_cast<float*>(big + A.off_zf);
+            const int zld = NP + 4;
+            auto zf_put = [&](int q8, const float (&zv)[8]) {
+                if (row >= NP) return;
+                float w8[8];
+    #pragma unroll
+                for (int u = 0; u < 8; ++u) w8[u] = (row < m && col0 + 8 * q8 + u < m) ? zv[u] : 0.f;
+                float4* dst = reinterpret_cast<float4*>(zf + row * zld + col0 + 8 * q8);
+                dst[0] = make_float4(w8[0], w8[1], w8[2], w8[3]);
+                dst[1] = make_float4(w8[4], w8[5], w8[6], w8[7]);
+            };
+            if (z_state == 2) {
+                tmem_rows(tl + TM_Z, nq, zf_put);
+            } else {
     #pragma unroll 1
                 for (int q8 = 0; q8 < nq; ++q8) {
                     float zv[8];
                     zrow(q8, zv);
-    #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (col0 + 8 * q8 + u < m) part += zv[u] * x_in[col0 + 8 * q8 + u];
+                    zf_put(q8, zv);
+                }
+            }
+            __syncthreads();
+            // y_out[row] = sum_j Z[row][j] x_in[j]  (all rows; rows >= m give 0)
+            auto zmatvec = [&](const float* x_in, float* y_out) {
+                float part = 0.f;
+                const float* zr = zf + (row < NP ? row : 0) * zld + col0;
+    #pragma unroll 2
+                for (int q4 = 0; q4 < half / 4; ++q4) {
+                    const float4 z4 = *reinterpret_cast<const float4*>(zr + 4 * q4);
+                    const float4 x4 = *reinterpret_cast<const float4*>(x_in + col0 + 4 * q4);
+                    const int j = col0 + 4 * q4;
+                    if (j < m) part += z4.x * x4.x;
+                    if (j + 1 < m) part += z4.y * x4.y;
+                    if (j + 2 < m) part += z4.z * x4.z;
+                    if (j + 3 < m) part += z4.w * x4.w;
                 }
                 vtmp[hh * 128 + row] = part;
                 __syncthreads();
@@ -1681,11 +1830,28 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             float* hv = vec + 1536;                  // 256: halo-actuator vector
             const int n_ref = s_scale > A.s_split ? 2 : 1;
             for (int ref = 0; ref < n_ref; ++ref) {
-                for (int j = warp; j < n_h; j += FT / 32) {        // h = X'_h w_bar
-                    float part = 0.f;
-                    for (int i = lane; i < m; i += 32) part += Xh[(size_t)j * A.m_pad + i] * wbar[i];
-                    part = warp_sum(part);
-                    if (lane == 0) hv[j] = part;
+                {                                                   // h = X'_h w_bar, two rows per warp pass
+                    float wr[4];
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u) wr[u] = lane + 32 * u < m ? wbar[lane + 32 * u] : 0.f;
+                    for (int j0 = warp; j0 < n_h; j0 += 2 * (FT / 32)) {
+                        const int j1 = j0 + FT / 32;
+                        float p0 = 0.f, p1 = 0.f;
+    #pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int i = lane + 32 * u;
+                            if (i < m) {
+                                p0 += Xh[(size_t)j0 * A.m_pad + i] * wr[u];
+                                if (j1 < n_h) p1 += Xh[(size_t)j1 * A.m_pad + i] * wr[u];
+                            }
+                        }
+                        p0 = warp_sum(p0);
+                        p1 = warp_sum(p1);
+                        if (lane == 0) {
+                            hv[j0] = p0;
+                            if (j1 < n_h) hv[j1] = p1;
+                        }
+                    }
                 }
                 __syncthreads();
                 for (int k = tid; k < p_loc; k += FT) {            // t = d/sigma - S w_bar, per slope
@@ -1697,15 +1863,13 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 }
                 __syncthreads();
                 for (int j = tid; j < n_h; j += FT) {              // g = D_loc^T t / sigma, per halo actuator
+                    // its (up to four) subapertures in increasing order: corners 11, 10, 01, 00
+                    const uchar4 v = inc4[j];
                     float g = 0.f;
-                    for (int s = 0; s < n_obs; ++s) {
-                        const int pc = pcs[s];
-                        const float tx = tvv[2 * s], ty = tvv[2 * s + 1];
-                        if ((pc & 0xFF) == j) g += -0.5f * tx - 0.5f * ty;
-                        if (((pc >> 8) & 0xFF) == j) g += 0.5f * tx - 0.5f * ty;
-                        if (((pc >> 16) & 0xFF) == j) g += -0.5f * tx + 0.5f * ty;
-                        if (((pc >> 24) & 0xFF) == j) g += 0.5f * tx + 0.5f * ty;
-                    }
+                    if (v.w != 0xFF) g += 0.5f * tvv[2 * v.w] + 0.5f * tvv[2 * v.w + 1];
+                    if (v.z != 0xFF) g += -0.5f * tvv[2 * v.z] + 0.5f * tvv[2 * v.z + 1];
+                    if (v.y != 0xFF) g += 0.5f * tvv[2 * v.y] - 0.5f * tvv[2 * v.y + 1];
+                    if (v.x != 0xFF) g += -0.5f * tvv[2 * v.x] - 0.5f * tvv[2 * v.x + 1];
                     hv[j] = g * A.inv_sigma;
                 }
                 __syncthreads();
@@ -1737,7 +1901,12 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
     #pragma unroll 1
             for (int q8 = 0; q8 < nq; ++q8) {
                 float zv[8], bv[8];
-                zrow(q8, zv);
+                {
+                    const float4* zr = reinterpret_cast<const float4*>(zf + (row < NP ? row : 0) * zld + col0 + 8 * q8);
+                    const float4 a0 = zr[0], a1 = zr[1];
+                    zv[0] = a0.x; zv[1] = a0.y; zv[2] = a0.z; zv[3] = a0.w;
+                    zv[4] = a1.x; zv[5] = a1.y; zv[6] = a1.z; zv[7] = a1.w;
+                }
     #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int j = col0 + 8 * q8 + u;
@@ -1773,15 +1942,22 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             tc_fence_after();
         }
         // ---- epilogue: analysis rows, forecast, prediction
-        auto prow = [&](int q8, float (&dv)[8]) {   // 8 columns of this thread's row of X'_E T
+        // f(q8, dv) over this thread's half-row of X'_E T, 8 columns at a time (tensor memory, two
+        // loads in flight, or the SIMT analysis's shared-memory rows)
+        auto over_row = [&](auto&& f) {
             if (simt) {
+#pragma unroll 1
+                for (int q8 = 0; q8 < nq; ++q8) {
+                    float dv[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = col0 + 8 * q8 + u;
-                    dv[u] = (row < n_e && j < m) ? sout[row * sld + j] : 0.f;
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = col0 + 8 * q8 + u;
+                        dv[u] = (row < n_e && j < m) ? sout[row * sld + j] : 0.f;
+                    }
+                    f(q8, dv);
                 }
             } else {
-                tmem_ld8(tl + TM_P + 8 * q8, dv);
+                tmem_rows(tl + TM_P, nq, f);
             }
         };
         const bool mine = row < n_e;
@@ -1792,14 +1968,11 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         }
         {   // member mean of this row of X'_E T (two column halves)
             float part = 0.f;
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float dv[8];
-                prow(q8, dv);
+            over_row([&](int q8, const float (&dv)[8]) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (col0 + 8 * q8 + u < m) part += dv[u];
-            }
+            });
             vtmp[hh * 128 + row] = part;
             __syncthreads();
         }
@@ -1810,51 +1983,92 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         const bool ar2 = A.with_forecast && A.a2 != 0.f;
         float* x2buf = reinterpret_cast<float*>(big);
         if (ar2) {
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float dv[8];
-                prow(q8, dv);
+            over_row([&](int q8, const float (&dv)[8]) {
                 if (mine && row >= n_own)
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
                         if (col0 + 8 * q8 + u < m) x2buf[(row - n_own) * A.m_pad + col0 + 8 * q8 + u] = shift + dv[u];
-            }
+            });
             __syncthreads();
         }
         const bool writes = mine && !(ar2 && row >= n_own);
         const bool dense_v = writes && A.with_forecast && A.vmode == 0;
         float psum = 0.f;
-#pragma unroll 1
-        for (int q8 = 0; q8 < nq; ++q8) {
-            float vq[8];     // this chunk's process noise, loaded before the tensor-memory read
+        // analysis rows, forecast and prediction sum for 8 columns: dv of X'_E T, vc of the noise
+        auto put = [&](int q8, const float (&dv)[8], const float (&vc)[8]) {
+            if (!writes) return;
+            const int c8 = col0 + 8 * q8, valid = m - c8;
+            if (valid <= 0) return;
+            float xa[8], n1[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int j = col0 + 8 * q8 + u;
-                vq[u] = (dense_v && j < m) ? A.V[(size_t)jact * A.m_pad + j] : 0.f;
+                const int j = c8 + u;
+                xa[u] = shift + dv[u];
+                if (A.with_forecast && j < m) {
+                    float v = 0.f;
+                    if (A.vmode == 0) {
+                        v = vc[u];
+                    } else if (A.vmode == 1) {
+                        float zz[4];
+                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
+                        v = A.q_white * zz[jact & 3];
+                    }
+                    n1[u] = A.a * xa[u] + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + v;
+                    psum += n1[u];
+                } else {
+                    n1[u] = 0.f;
+                }
             }
-            float dv[8];
-            prow(q8, dv);
-            if (!writes) continue;
+            if (A.with_forecast) {
+                put8(A.Xo + (size_t)jact * A.m_pad + c8, n1, valid);
+                put8(A.Xo + (size_t)(A.n_act + jact) * A.m_pad + c8, xa, valid);
+            } else {
+                put8(A.Xo + (size_t)grow * A.m_pad + c8, xa, valid);
+            }
+        };
+        const float* vrow = A.V + (size_t)jact * A.m_pad + col0;
+        auto vload = [&](int q8, float (&v)[8]) {
+            if (dense_v) get8(vrow + 8 * q8, v, m - col0 - 8 * q8);
+            else
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = col0 + 8 * q8 + u;
-                if (j < m) {
-                    const float xa = shift + dv[u];
-                    if (A.with_forecast) {
-                        float v = 0.f;
-                        if (A.vmode == 0) {
-                            v = vq[u];
-                        } else if (A.vmode == 1) {
-                            float zz[4];
-                            normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
-                            v = A.q_white * zz[jact & 3];
-                        }
-                        const float n1 = A.a * xa + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + v;
-                        A.Xo[(size_t)jact * A.m_pad + j] = n1;
-                        A.Xo[(size_t)(A.n_act + jact) * A.m_pad + j] = xa;
-                        psum += n1;
-                    } else {
-                        A.Xo[(size_t)grow * A.m_pad + j] = xa;
+                for (int u = 0; u < 8; ++u) v[u] = 0.f;
+        };
+        if (simt) {
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float dv[8], vc[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = col0 + 8 * q8 + u;
+                    dv[u] = (row < n_e && j < m) ? sout[row * sld + j] : 0.f;
+                }
+                vload(q8, vc);
+                put(q8, dv, vc);
+            }
+        } else {
+            // the next chunk's tensor-memory load and noise loads are in flight while this one is
+            // written
+            uint32_t rc[8], rn[8];
+            float vc[8], vn[8];
+            vload(0, vc);
+            tmem_ld8_async(tl + TM_P, rc);
+            tmem_wait_ld(rc);
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                if (q8 + 1 < nq) {
+                    vload(q8 + 1, vn);
+                    tmem_ld8_async(tl + TM_P + 8 * (q8 + 1), rn);
+                }
+                float dv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) dv[u] = __uint_as_float(rc[u]);
+                put(q8, dv, vc);
+                if (q8 + 1 < nq) {
+                    tmem_wait_ld(rn);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        rc[u] = rn[u];
+                        vc[u] = vn[u];
                     }
                 }
             }
@@ -1977,7 +2191,7 @@ __global__ void wait_selftest_kernel(long long limit, int arrive, int* status) {
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 struct FusedLayout {
-    int NP, KP, RA, sz_op, sz_opg, sz_a, off_vec, off_xe, off_xh, off_big, total;
+    int NP, KP, RA, sz_op, sz_opg, sz_a, off_vec, off_xe, off_xh, off_big, off_zf = 0, total;
 };
 
 // Ensembles of m >= 128 members do not fit one 128-row MMA tile: they take the dual form.
@@ -2017,7 +2231,9 @@ FusedLayout fused_layout(const letkf_ctx* c) {
     L.off_xh = L.off_xe + xe_bytes;
     const int xh_bytes = round_up(std::max(h.n_h_max, 1) * c->m_pad * 4, 1024);
     L.off_big = L.off_xh + xh_bytes;
-    int big = std::max(2 * L.sz_opg, std::max(6 * L.sz_op, 2 * L.sz_a + 2 * L.sz_op));
+    L.off_zf = round_up(2 * L.sz_a + 2 * L.sz_op, 1024);       // past the transform's operands
+    const int zf_bytes = L.NP * (L.NP + 4) * 4;
+    int big = std::max(std::max(2 * L.sz_opg, std::max(6 * L.sz_op, 2 * L.sz_a + 2 * L.sz_op)), L.off_zf + zf_bytes);
     big += (MT - std::min(L.NP, L.RA)) * std::max(L.KP, L.NP) * 2;   // rows a 128-row MMA reads past the end
     L.total = L.off_big + round_up(big, 1024);
     if (c->simt_q > 0) L.total = std::max(L.total, L.off_big + round_up(c->simt_ws, 1024));
@@ -2185,6 +2401,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->sz_op = L.sz_op;
     S->sz_opg = L.sz_opg;
     S->sz_a = L.sz_a;
+    S->off_zf = L.off_zf;
     S->cap = c->cap_dev;
     S->cap_dom = c->cap_dom;
 }
