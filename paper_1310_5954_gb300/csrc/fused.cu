@@ -89,6 +89,7 @@ struct SysDesc {
     // for every system, so a region below off_big never overlaps another system's operands
     int off_vec, off_xe, off_xh, off_big, sz_op, sz_opg, sz_a;
     int off_zf;          // m x m form: FP32 rows of Z in the big region, past the transform's operands
+    int off_vs;          // m x m form: the domain's rows of the process noise V (in the big region), or -1
     // test instrument: when cap is set, the analysis of domain cap_dom writes what it computed
     // (header, mean weights, transform or its factors; layout in letkf_set_capture) to cap
     float* cap;
@@ -258,6 +259,14 @@ __device__ __forceinline__ void tmem_rows(uint32_t taddr, int nq, F&& f) {
         }
     }
 }
+
+// 16 bytes global -> shared without holding registers (completion: cp_async_wait_all, then a
+// barrier before other threads read them).
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // 8 consecutive floats of a row in global memory, of which the first `valid` exist (16-byte aligned
 // at dst): two 16-byte accesses when all 8 do, else element by element.  A warp's threads write
@@ -1425,10 +1434,17 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         if (warp == 0 && !A.dual && !ctl->loaded) issue_loads(A, d, smem, &ctl->bar_load);
         // ---- frame ingest: a non-finite slope in this domain's observation region rejects the
         //      system's frame (its state is restored when the launch ends)
+        // (the m x m forms keep the region's slopes in shared memory for the innovation row)
+        float* ys = vec + 1856;          // 128: x and y slope of each observed subaperture
         int nonfinite = 0;
         for (int t = tid; t < n_obs; t += FT) {
             const int sub = A.tab.obs_sub[o0 + t];
-            if (!isfinite(A.y[sub]) || !isfinite(A.y[A.n_subv + sub])) nonfinite = 1;
+            const float yx = A.y[sub], yy = A.y[A.n_subv + sub];
+            if (!isfinite(yx) || !isfinite(yy)) nonfinite = 1;
+            if (!A.dual) {
+                ys[2 * t] = yx;
+                ys[2 * t + 1] = yy;
+            }
         }
         const bool dom_bad = __syncthreads_or(nonfinite) != 0;
         if (A.dual) {
@@ -1490,8 +1506,10 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             }
         }
         int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
+        int* owns = reinterpret_cast<int*>(vec + 1984);  // 64: its own actuators
         uchar4* inc4 = reinterpret_cast<uchar4*>(xh_mean);   // over the halo means once they are used
         for (int t = tid; t < n_obs; t += FT) pcs[t] = A.tab.obs_corner[o0 + t];
+        for (int t = tid; t < n_own; t += FT) owns[t] = A.tab.own[e0 + t];
         __syncthreads();
         // ---- small domains: the FP32 SIMT analysis leaves X'_E T in shared memory
         const bool simt = A.simt_q > 0 && min(p_loc, m) <= A.simt_q;
@@ -1500,8 +1518,8 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         if (simt) {
             sout = analyse_simt(B, ctl, smem, d, &sld);
         } else {
-            for (int t = tid; t < NP * (KP >> 3); t += FT) {
-                const int i = t % NP, kc = t / NP;
+            // thread (i = tid mod 128, kc = tid / 128 + 2 k): row i of the operand, 8 K-values per task
+            for (int kc = tid >> 7, i = tid & 127; i < NP && kc < (KP >> 3); kc += 2) {
                 float v[8];
     #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1523,9 +1541,8 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                             sx *= A.inv_sigma;
                             sy *= A.inv_sigma;
                         } else {
-                            const int sub = A.tab.obs_sub[o0 + sidx];
-                            sx = (A.y[sub] - sx) * A.inv_sigma;
-                            sy = (A.y[A.n_subv + sub] - sy) * A.inv_sigma;
+                            sx = (ys[2 * sidx] - sx) * A.inv_sigma;
+                            sy = (ys[2 * sidx + 1] - sy) * A.inv_sigma;
                             dtv[2 * sidx] = sx;
                             dtv[2 * sidx + 1] = sy;
                         }
@@ -1751,6 +1768,18 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
+            // the domain's rows of the process noise V, copied to shared memory now for the epilogue
+            // (its global rows may sit in the other die's memory: a latency the analysis hides)
+            const bool vstage = A.with_forecast && A.vmode == 0 && A.off_vs >= 0;
+            float* vs = reinterpret_cast<float*>(big + (A.off_vs >= 0 ? A.off_vs : 0));
+            if (vstage) {
+                const int q4 = A.m_pad >> 2;
+                for (int t = tid; t < n_own * q4; t += FT) {
+                    const int e = t / q4, c4 = t - e * q4;
+                    cp_async16(vs + e * A.m_pad + 4 * c4, A.V + (size_t)owns[e] * A.m_pad + 4 * c4);
+                }
+                cp_async_commit();
+            }
             // ---- 4. mean weights w_bar = Z (Z b) / (c s), refined against the exact operator
             // 8 columns of this thread's half-row of Z = A_s^(-1/2)
             auto zrow = [&](int q8, float (&zv)[8]) {
@@ -1963,19 +1992,45 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         const bool mine = row < n_e;
         int grow = 0, jact = 0;
         if (mine) {
-            jact = row < n_own ? A.tab.own[e0 + row] : A.tab.own[e0 + row - n_own];
+            jact = row < n_own ? owns[row] : owns[row - n_own];
             grow = row < n_own ? jact : A.n_act + jact;
         }
+        // the tensor-core product is read from tensor memory once: its rows go to shared memory
+        // (FP32, row stride NP + 4, over Z's rows, which the transform no longer needs) for the
+        // passes below
+        float* pst = reinterpret_cast<float*>(big + A.off_zf);
+        const int pld = NP + 4;
+        const bool vsm = !simt && A.with_forecast && A.vmode == 0 && A.off_vs >= 0;   // V rows staged
+        if (vsm) cp_async_wait_all();   // this thread's copies; the barrier below publishes them all
         {   // member mean of this row of X'_E T (two column halves)
             float part = 0.f;
             over_row([&](int q8, const float (&dv)[8]) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (col0 + 8 * q8 + u < m) part += dv[u];
+                if (!simt && mine) {
+                    float4* dst = reinterpret_cast<float4*>(pst + row * pld + col0 + 8 * q8);
+                    dst[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                    dst[1] = make_float4(dv[4], dv[5], dv[6], dv[7]);
+                }
             });
             vtmp[hh * 128 + row] = part;
             __syncthreads();
         }
+        // 8 columns of this thread's row of X'_E T from shared memory (after the pass above)
+        auto srow = [&](int q8, float (&dv)[8]) {
+            if (simt) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = col0 + 8 * q8 + u;
+                    dv[u] = (row < n_e && j < m) ? sout[row * sld + j] : 0.f;
+                }
+            } else {
+                const float4* src = reinterpret_cast<const float4*>(pst + (mine ? row : 0) * pld + col0 + 8 * q8);
+                const float4 a = src[0], b = src[1];
+                dv[0] = a.x; dv[1] = a.y; dv[2] = a.z; dv[3] = a.w; dv[4] = b.x; dv[5] = b.y; dv[6] = b.z; dv[7] = b.w;
+            }
+        };
         const float shift = mine ? xe_mean[row] + uvec[row] - (vtmp[row] + vtmp[128 + row]) / (float)m : 0.f;
         __syncthreads();
         // AR(2) forecast: the rows of the second instant leave their analysis in shared memory (the
@@ -1983,12 +2038,15 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
         const bool ar2 = A.with_forecast && A.a2 != 0.f;
         float* x2buf = reinterpret_cast<float*>(big);
         if (ar2) {
-            over_row([&](int q8, const float (&dv)[8]) {
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float dv[8];
+                srow(q8, dv);
                 if (mine && row >= n_own)
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
                         if (col0 + 8 * q8 + u < m) x2buf[(row - n_own) * A.m_pad + col0 + 8 * q8 + u] = shift + dv[u];
-            });
+            }
             __syncthreads();
         }
         const bool writes = mine && !(ar2 && row >= n_own);
@@ -2005,15 +2063,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 const int j = c8 + u;
                 xa[u] = shift + dv[u];
                 if (A.with_forecast && j < m) {
-                    float v = 0.f;
-                    if (A.vmode == 0) {
-                        v = vc[u];
-                    } else if (A.vmode == 1) {
-                        float zz[4];
-                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
-                        v = A.q_white * zz[jact & 3];
-                    }
-                    n1[u] = A.a * xa[u] + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + v;
+                    n1[u] = A.a * xa[u] + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + vc[u];
                     psum += n1[u];
                 } else {
                     n1[u] = 0.f;
@@ -2026,51 +2076,46 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                 put8(A.Xo + (size_t)grow * A.m_pad + c8, xa, valid);
             }
         };
-        const float* vrow = A.V + (size_t)jact * A.m_pad + col0;
+        const float* vrow = vsm ? reinterpret_cast<const float*>(big + A.off_vs) +
+                                      (size_t)(row < n_own ? row : row - n_own) * A.m_pad + col0
+                                : A.V + (size_t)jact * A.m_pad + col0;
+        // the process noise of 8 columns: V's rows, or white noise drawn here (kept out of the
+        // unrolled arithmetic above: its Philox code inlined there cost instruction-cache misses)
+        const bool white_v = writes && A.with_forecast && A.vmode == 1;
         auto vload = [&](int q8, float (&v)[8]) {
-            if (dense_v) get8(vrow + 8 * q8, v, m - col0 - 8 * q8);
-            else
+            if (dense_v) {
+                get8(vrow + 8 * q8, v, m - col0 - 8 * q8);
+            } else {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = 0.f;
-        };
-        if (simt) {
+                if (white_v)
 #pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float dv[8], vc[8];
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = col0 + 8 * q8 + u;
+                        if (j < m) {
+                            float zz[4];
+                            normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
+                            const float w = A.q_white * zz[jact & 3];
+                            // a register array indexed by a runtime u would live in local memory
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = col0 + 8 * q8 + u;
-                    dv[u] = (row < n_e && j < m) ? sout[row * sld + j] : 0.f;
-                }
-                vload(q8, vc);
-                put(q8, dv, vc);
+                            for (int k = 0; k < 8; ++k)
+                                if (k == u) v[k] = w;
+                        }
+                    }
             }
-        } else {
-            // the next chunk's tensor-memory load and noise loads are in flight while this one is
-            // written
-            uint32_t rc[8], rn[8];
+        };
+        {   // the next chunk's noise loads are in flight while this one is written
             float vc[8], vn[8];
             vload(0, vc);
-            tmem_ld8_async(tl + TM_P, rc);
-            tmem_wait_ld(rc);
 #pragma unroll 1
             for (int q8 = 0; q8 < nq; ++q8) {
-                if (q8 + 1 < nq) {
-                    vload(q8 + 1, vn);
-                    tmem_ld8_async(tl + TM_P + 8 * (q8 + 1), rn);
-                }
+                if (q8 + 1 < nq) vload(q8 + 1, vn);
                 float dv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) dv[u] = __uint_as_float(rc[u]);
+                srow(q8, dv);
                 put(q8, dv, vc);
-                if (q8 + 1 < nq) {
-                    tmem_wait_ld(rn);
+                if (q8 + 1 < nq)
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        rc[u] = rn[u];
-                        vc[u] = vn[u];
-                    }
-                }
+                    for (int u = 0; u < 8; ++u) vc[u] = vn[u];
             }
         }
         if (A.with_forecast) {
@@ -2191,7 +2236,7 @@ __global__ void wait_selftest_kernel(long long limit, int arrive, int* status) {
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 struct FusedLayout {
-    int NP, KP, RA, sz_op, sz_opg, sz_a, off_vec, off_xe, off_xh, off_big, off_zf = 0, total;
+    int NP, KP, RA, sz_op, sz_opg, sz_a, off_vec, off_xe, off_xh, off_big, off_zf = 0, off_vs = -1, total;
 };
 
 // Ensembles of m >= 128 members do not fit one 128-row MMA tile: they take the dual form.
@@ -2232,9 +2277,17 @@ FusedLayout fused_layout(const letkf_ctx* c) {
     const int xh_bytes = round_up(std::max(h.n_h_max, 1) * c->m_pad * 4, 1024);
     L.off_big = L.off_xh + xh_bytes;
     L.off_zf = round_up(2 * L.sz_a + 2 * L.sz_op, 1024);       // past the transform's operands
-    const int zf_bytes = L.NP * (L.NP + 4) * 4;
+    // Z's FP32 rows, and in the epilogue the rows of X'_E T (at most RA of them)
+    const int zf_bytes = std::max(L.NP, L.RA) * (L.NP + 4) * 4;
     int big = std::max(std::max(2 * L.sz_opg, std::max(6 * L.sz_op, 2 * L.sz_a + 2 * L.sz_op)), L.off_zf + zf_bytes);
+    // the own rows of V (first instant), past Z's rows, when it fits shared memory
+    const int off_vs = round_up(L.off_zf + zf_bytes, 128);
+    const int vs_bytes = std::max(h.n_loc_max / 2, 1) * c->m_pad * 4;
     big += (MT - std::min(L.NP, L.RA)) * std::max(L.KP, L.NP) * 2;   // rows a 128-row MMA reads past the end
+    if (L.off_big + round_up(std::max(big, off_vs + vs_bytes), 1024) <= 227 * 1024) {
+        L.off_vs = off_vs;
+        big = std::max(big, off_vs + vs_bytes);
+    }
     L.total = L.off_big + round_up(big, 1024);
     if (c->simt_q > 0) L.total = std::max(L.total, L.off_big + round_up(c->simt_ws, 1024));
     return L;
@@ -2402,6 +2455,7 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->sz_opg = L.sz_opg;
     S->sz_a = L.sz_a;
     S->off_zf = L.off_zf;
+    S->off_vs = L.off_vs;
     S->cap = c->cap_dev;
     S->cap_dom = c->cap_dom;
 }
