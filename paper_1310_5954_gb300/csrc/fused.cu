@@ -763,10 +763,13 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         for (int t = tid; t < m; t += FT) A.cap[CAP_HDR + t] = wbar[t];
     }
     // ---- (I + Z)^-1, Z = Z_ns / sqrt(s), by Newton's iteration X <- X (2I - (I + Z) X) from
-    //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G
+    //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G.
+    //      The first step is elementwise, X_1 = 4/3 I - 4/9 (I + Z); the residual R = I - M X
+    //      squares at every step, so once ||R||_F^2 is under the stopping bound the update is the
+    //      last and the product that would confirm it is skipped.
     const float rs = rsqrtf(s_ns);
 #pragma unroll 1
-    for (int q8 = 0; q8 < nq; ++q8) {               // M = I + Z into Y's buffers, X_0 into T's
+    for (int q8 = 0; q8 < nq; ++q8) {               // M = I + Z into Y's buffers, X_1 into T's
         float zv[8], mv[8], xv[8];
         zrow(q8, zv);
 #pragma unroll
@@ -775,7 +778,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             const bool in = row < P && j < P;
             const float id = (row == j) ? 1.f : 0.f;
             mv[u] = in ? id + zv[u] * rs : 0.f;
-            xv[u] = in ? (2.f / 3.f) * id : 0.f;
+            xv[u] = in ? (4.f / 3.f) * id - (4.f / 9.f) * mv[u] : 0.f;
         }
         if (row < NP) {
             store8(Yh, Yl, row, col0 + 8 * q8, NP, mv, true);
@@ -808,6 +811,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
         r2 = block_sum(ctl, r2);
         if (sqrtf(r2) < 1e-6f * (float)P) break;
+        const bool last = r2 < 1e-6f * (float)P;     // the update lands ||R||_F under the bound
         to_mma();
         if (tid == 0) {
             tc_fence_after();
@@ -815,13 +819,14 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             mma_commit(&ctl->bar_mma);
         }
         if (!mma_wait()) return false;
+        x_in_tmem = true;
+        if (last) break;                            // X stays in tensor memory
 #pragma unroll 1
         for (int q8 = 0; q8 < nq; ++q8) {
             float xv[8];
             tmem_ld8(tl + TM_G + 8 * q8, xv);
             if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, xv, true);
         }
-        x_in_tmem = true;
         to_mma();
     }
     tc_fence_before();
@@ -908,9 +913,14 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         float xv[8];
         if (x_in_tmem) {
             tmem_ld8(tl + TM_G + 8 * q8, xv);
-        } else {
+        } else {                                    // X_1 = 4/3 I - 4/9 (I + Z)
+            float zv[8];
+            zrow(q8, zv);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) xv[u] = (row == col0 + 8 * q8 + u) ? 2.f / 3.f : 0.f;
+            for (int u = 0; u < 8; ++u) {
+                const float id = (row == col0 + 8 * q8 + u) ? 1.f : 0.f;
+                xv[u] = (4.f / 3.f) * id - (4.f / 9.f) * (id + zv[u] * rs);
+            }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) xv[u] = (row < P && col0 + 8 * q8 + u < P) ? xv[u] : 0.f;
