@@ -271,6 +271,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 8 consecutive floats of a row in global memory, of which the first `valid` exist (16-byte aligned
 // at dst): two 16-byte accesses when all 8 do, else element by element.  A warp's threads write
 // different rows, so vector accesses cut the number of scattered sectors by four.
+// Component k (a constant after unrolling) of v.
+__device__ __forceinline__ float f4c(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
 __device__ __forceinline__ void put8(float* dst, const float (&v)[8], int valid) {
     if (valid >= 8) {
         reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -510,28 +513,47 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         __syncthreads();
     };
 
-    // ---- halo anomalies of the observed instant (FP32) into the scratch
-    for (int j = warp; j < n_h; j += FT / 32) {
-        const float* x = A.X + (size_t)(A.row_obs + A.tab.halo[h0 + j]) * A.m_pad;
+    // ---- halo anomalies of the observed instant (FP32) into the scratch: sixteen lanes per row and
+    //      four members per load, 16 rows per pass; the padding columns m .. m_pad are written as 0
+    const int nq4 = A.m_pad >> 2;                   // <= 64
+    const int g8 = lane >> 3, l8 = lane & 7;
+    float4* Xs4 = reinterpret_cast<float4*>(Xs);
+    for (int j0 = 2 * warp; j0 < n_h; j0 += FT / 16) {
+        const int j = j0 + (lane >> 4), l16 = lane & 15;
+        const bool has = j < n_h;
+        const float4* x = reinterpret_cast<const float4*>(A.X + (size_t)(A.row_obs + A.tab.halo[h0 + (has ? j : 0)]) * A.m_pad);
+        float4 v[4];
         float sm_ = 0.f;
-        for (int i = lane; i < m; i += 32) sm_ += x[i];
-        sm_ = warp_sum(sm_);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = l16 + 16 * u;
+            v[u] = (has && q < nq4) ? x[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * q + 0 >= m) v[u].x = 0.f;
+            if (4 * q + 1 >= m) v[u].y = 0.f;
+            if (4 * q + 2 >= m) v[u].z = 0.f;
+            if (4 * q + 3 >= m) v[u].w = 0.f;
+            sm_ += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) sm_ += __shfl_xor_sync(0xffffffffu, sm_, o);
         const float mu = sm_ / (float)m;
-        for (int i = lane; i < m; i += 32) Xs[(size_t)j * A.m_pad + i] = x[i] - mu;
-        if (lane == 0) xh_mean[j] = mu;
+        if (has) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = l16 + 16 * u;
+                if (q < nq4)
+                    Xs4[(size_t)j * nq4 + q] = make_float4(4 * q + 0 < m ? v[u].x - mu : 0.f, 4 * q + 1 < m ? v[u].y - mu : 0.f,
+                                                           4 * q + 2 < m ? v[u].z - mu : 0.f, 4 * q + 3 < m ? v[u].w - mu : 0.f);
+            }
+            if (l16 == 0) xh_mean[j] = mu;
+        }
     }
+    float* hv = vec + 1536;                          // 256: halo-actuator vector
+    int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
+    for (int s = tid; s < n_obs; s += FT) pcs[s] = A.tab.obs_corner[o0 + s];
     __syncthreads();
-    auto slope_at = [&](int k, int i) -> float {    // S[k][i], k = 2 s + direction
-        const int pc = A.tab.obs_corner[o0 + (k >> 1)];
-        const float a00 = Xs[(size_t)(pc & 0xFF) * A.m_pad + i];
-        const float a01 = Xs[(size_t)((pc >> 8) & 0xFF) * A.m_pad + i];
-        const float a10 = Xs[(size_t)((pc >> 16) & 0xFF) * A.m_pad + i];
-        const float a11 = Xs[(size_t)((pc >> 24) & 0xFF) * A.m_pad + i];
-        const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
-        return sl * A.inv_sigma;
-    };
     for (int k = tid; k < P; k += FT) {             // innovation d / sigma
-        const int pc = A.tab.obs_corner[o0 + (k >> 1)];
+        const int pc = pcs[k >> 1];
         const float a00 = xh_mean[pc & 0xFF], a01 = xh_mean[(pc >> 8) & 0xFF];
         const float a10 = xh_mean[(pc >> 16) & 0xFF], a11 = xh_mean[(pc >> 24) & 0xFF];
         const float sl = (k & 1) == 0 ? 0.5f * ((a01 + a11) - (a00 + a10)) : 0.5f * ((a10 + a11) - (a00 + a01));
@@ -539,17 +561,35 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         const float yv = (k & 1) == 0 ? A.y[sub] : A.y[A.n_subv + sub];
         dvec[k] = (yv - sl) * A.inv_sigma;
     }
-    // S as an NP x MP operand (rows: slopes, K: members)
+    // S as an NP x MP operand (rows: slopes, K: members): both slopes of a subaperture from one
+    //      read of its four corners' anomalies, eight members at a time
     auto write_S = [&](unsigned char* hi, unsigned char* lo) {
-        for (int t = tid; t < NP * (MP >> 3); t += FT) {
-            const int k = t % NP, ic = t / NP;
-            float v[8];
+        const int ns2 = NP >> 1;
+        for (int t = tid; t < ns2 * (MP >> 3); t += FT) {
+            const int sb = t % ns2, ic = t / ns2;
+            float vx[8], vy[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = ic * 8 + u;
-                v[u] = (k < P && i < m) ? slope_at(k, i) : 0.f;
+            for (int u = 0; u < 8; ++u) vx[u] = vy[u] = 0.f;
+            if (sb < n_obs) {
+                const int pc = pcs[sb];
+                float4 c[4][2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4* r = Xs4 + (size_t)((pc >> (8 * q)) & 0xFF) * nq4 + 2 * ic;
+                    c[q][0] = 8 * ic + 4 <= A.m_pad ? r[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    c[q][1] = 8 * ic + 8 <= A.m_pad ? r[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float a00 = f4c(c[0][u >> 2], u & 3), a01 = f4c(c[1][u >> 2], u & 3);
+                    const float a10 = f4c(c[2][u >> 2], u & 3), a11 = f4c(c[3][u >> 2], u & 3);
+                    const bool in = ic * 8 + u < m;
+                    vx[u] = in ? 0.5f * ((a01 + a11) - (a00 + a10)) * A.inv_sigma : 0.f;
+                    vy[u] = in ? 0.5f * ((a10 + a11) - (a00 + a01)) * A.inv_sigma : 0.f;
+                }
             }
-            store8(hi, lo, k, ic * 8, MP, v, true);
+            store8(hi, lo, 2 * sb, ic * 8, MP, vx, true);
+            store8(hi, lo, 2 * sb + 1, ic * 8, MP, vy, true);
         }
     };
     unsigned char* Sg_h = big;
@@ -590,10 +630,13 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
     const float inv_cs = 1.f / (c * s_ns);
     const float ns_last = ns_stop(A.ns_last, A.gram_terms, s_scale, A.s_split);
-    // ---- Z = ((I + K/c)/s)^(-1/2) by the coupled Newton-Schulz iteration (dimension P)
+    // ---- Z = ((I + K/c)/s)^(-1/2) by the coupled Newton-Schulz iteration (dimension P), from
+    //      Y_0 = A_s, Z_0 = I: the first step's P_0 = Z_0 Y_0 is Y_0 itself, so one pass over G
+    //      writes Y_0, T_0 = (3I - Y_0)/2, Z_0 and the residual, and the step's two products follow
+    float r2_0 = 0.f;
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {
-        float g[8], yv[8], zv[8];
+        float g[8], yv[8], zv[8], tv[8];
         tmem_ld8(tl + TM_G + 8 * q8, g);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -602,16 +645,46 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             const float id = (row == j) ? 1.f : 0.f;
             yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
             zv[u] = in ? id : 0.f;
+            tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
+            if (in) r2_0 += (id - yv[u]) * (id - yv[u]);
         }
         if (row < NP) {
             store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
             store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
+            store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
         }
     }
-    to_mma();
-    bool z_in_tmem = false;
-    float rn_prev = 3.0e38f;
+    float rn_prev = sqrtf(block_sum(ctl, r2_0));
+    bool z_in_tmem = false, more = false;
     int it = 0;
+    if (rn_prev >= 2e-6f * (float)P) {   // else converged at once: Z = I
+        to_mma();
+        const bool last0 = rn_prev < ns_last;
+        if (tid == 0) {
+            tc_fence_after();
+            if (!last0) issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
+            issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);                 // Z_1 = T_0
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!mma_wait()) return false;
+        z_in_tmem = true;
+        if (!last0) {                    // else the update was the last: Z_1 = T_0
+            it = 1;
+            more = true;
+#pragma unroll 1
+            for (int q8 = 0; q8 < nq; ++q8) {
+                float yv[8], zv[8];
+                tmem_ld8(tl + TM_Y + 8 * q8, yv);
+                tmem_ld8(tl + TM_Z + 8 * q8, zv);
+                if (row < NP) {
+                    store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                    store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
+                }
+            }
+            to_mma();
+        }
+    }
+    if (more)
     for (; it < A.max_it; ++it) {
         if (tid == 0) {
             tc_fence_after();
@@ -701,48 +774,89 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     // S = D_loc X'_h / sigma is linear in the halo anomalies: S^T u is X'_h^T applied to the
     // stencil's transpose of u, and S w the stencil of X'_h w (n_h x m products over the scratch
     // instead of four scratch loads per slope and member)
-    float* hv = vec + 1536;                          // 256: halo-actuator vector
-    int* pcs = reinterpret_cast<int*>(vec + 1792);   // 64: the domain's packed corners
-    for (int s = tid; s < n_obs; s += FT) pcs[s] = A.tab.obs_corner[o0 + s];
-    __syncthreads();
+    // (used between the two iterations, while the big region is free: partial sums and the
+    // incidence of each halo actuator, the subaperture of which it is corner (r, c), (r, c + 1),
+    // (r + 1, c), (r + 1, c + 1), 0xFF for none)
+    float4* part4 = reinterpret_cast<float4*>(big);               // FT float4
+    uchar4* inc4 = reinterpret_cast<uchar4*>(big + FT * 16);      // n_h <= 256
+    const int nch = FT / nq4, rows_ch = (n_h + nch - 1) / nch;
     auto st_times = [&](const float* u_in, float* w_out) {    // w = S^T u (members)
-        for (int j = tid; j < n_h; j += FT) {                  // g = D_loc^T u / sigma
+        for (int j = tid; j < n_h; j += FT) {                  // g = D_loc^T u / sigma, by incidence
+            const uchar4 ic = inc4[j];
             float g = 0.f;
-            for (int s = 0; s < n_obs; ++s) {
-                const int pc = pcs[s];
-                const float tx = u_in[2 * s], ty = u_in[2 * s + 1];
-                if ((pc & 0xFF) == j) g += -0.5f * tx - 0.5f * ty;
-                if (((pc >> 8) & 0xFF) == j) g += 0.5f * tx - 0.5f * ty;
-                if (((pc >> 16) & 0xFF) == j) g += -0.5f * tx + 0.5f * ty;
-                if (((pc >> 24) & 0xFF) == j) g += 0.5f * tx + 0.5f * ty;
-            }
+            if (ic.x != 0xFF) g += -0.5f * u_in[2 * ic.x] - 0.5f * u_in[2 * ic.x + 1];
+            if (ic.y != 0xFF) g += 0.5f * u_in[2 * ic.y] - 0.5f * u_in[2 * ic.y + 1];
+            if (ic.z != 0xFF) g += -0.5f * u_in[2 * ic.z] + 0.5f * u_in[2 * ic.z + 1];
+            if (ic.w != 0xFF) g += 0.5f * u_in[2 * ic.w] + 0.5f * u_in[2 * ic.w + 1];
             hv[j] = g * A.inv_sigma;
         }
         __syncthreads();
-        for (int i = tid; i < m; i += FT) {
-            float acc = 0.f;
+        {   // w = X'_h^T g: four members per thread over a chunk of rows, then the chunks' sum
+            const int q = tid % nq4, ch = tid / nq4;
+            if (ch < nch) {
+                const int ja = ch * rows_ch, jb = min(n_h, ja + rows_ch);
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-            for (int j = 0; j < n_h; ++j) acc += Xs[(size_t)j * A.m_pad + i] * hv[j];
-            w_out[i] = acc;
+                for (int j = ja; j < jb; ++j) {
+                    const float4 x = Xs4[(size_t)j * nq4 + q];
+                    const float h = hv[j];
+                    acc.x = fmaf(x.x, h, acc.x);
+                    acc.y = fmaf(x.y, h, acc.y);
+                    acc.z = fmaf(x.z, h, acc.z);
+                    acc.w = fmaf(x.w, h, acc.w);
+                }
+                part4[ch * nq4 + q] = acc;
+            }
+            __syncthreads();
+            for (int q4 = tid; q4 < nq4; q4 += FT) {
+                float4 s4 = part4[q4];
+                for (int c2 = 1; c2 < nch; ++c2) {
+                    const float4 t4 = part4[c2 * nq4 + q4];
+                    s4.x += t4.x;
+                    s4.y += t4.y;
+                    s4.z += t4.z;
+                    s4.w += t4.w;
+                }
+                reinterpret_cast<float4*>(w_out)[q4] = s4;
+            }
+            __syncthreads();
+        }
+    };
+    auto xh_times = [&](const float* w_in, float* h_out) {    // h = X'_h w: eight lanes per row
+        for (int j0 = 4 * warp; j0 < n_h; j0 += FT / 8) {
+            const int j = j0 + g8;
+            float part = 0.f;
+            if (j < n_h) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = l8 + 8 * u;
+                    if (q < nq4) {
+                        const float4 x = Xs4[(size_t)j * nq4 + q], w4 = reinterpret_cast<const float4*>(w_in)[q];
+                        part += (x.x * w4.x + x.y * w4.y) + (x.z * w4.z + x.w * w4.w);
+                    }
+                }
+            }
+            part += __shfl_xor_sync(0xffffffffu, part, 4);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            if (l8 == 0 && j < n_h) h_out[j] = part;
         }
         __syncthreads();
     };
     // ---- mean weights: u = Z_ns (Z_ns d) / (c s), refined against the exact FP32 slopes;
     //      w_bar = S^T u
-    zmatvec(dvec, vv);
+    for (int j = tid; j < n_h; j += FT) inc4[j] = make_uchar4(0xFF, 0xFF, 0xFF, 0xFF);
+    __syncthreads();
+    for (int t = tid; t < 4 * n_obs; t += FT)
+        reinterpret_cast<unsigned char*>(inc4 + ((pcs[t >> 2] >> (8 * (t & 3))) & 0xFF))[t & 3] = (unsigned char)(t >> 2);
+    zmatvec(dvec, vv);                               // (its barriers order the incidence writes)
     zmatvec(vv, uvp);
     if (hh == 0) uvp[row] = row < P ? uvp[row] * inv_cs : 0.f;
     __syncthreads();
     const int n_ref = s_scale > A.s_split ? 2 : 1;
     for (int ref = 0; ref < n_ref; ++ref) {
         st_times(uvp, wbar);                                   // S^T u
-        for (int j = warp; j < n_h; j += FT / 32) {            // h = X'_h (S^T u)
-            float part = 0.f;
-            for (int i = lane; i < m; i += 32) part += Xs[(size_t)j * A.m_pad + i] * wbar[i];
-            part = warp_sum(part);
-            if (lane == 0) hv[j] = part;
-        }
-        __syncthreads();
+        xh_times(wbar, hv);                                    // h = X'_h (S^T u)
         for (int k = tid; k < P; k += FT) {                    // rho = d - c u - S (S^T u)
             const int pc = pcs[k >> 1];
             const float a00 = hv[pc & 0xFF], a01 = hv[(pc >> 8) & 0xFF];
@@ -766,7 +880,8 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G.
     //      The first step is elementwise, X_1 = 4/3 I - 4/9 (I + Z); the residual R = I - M X
     //      squares at every step, so once ||R||_F^2 is under the stopping bound the update is the
-    //      last and the product that would confirm it is skipped.
+    //      last and the product that would confirm it is skipped.  At least one update runs, so X
+    //      ends in tensor memory.
     const float rs = rsqrtf(s_ns);
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {               // M = I + Z into Y's buffers, X_1 into T's
@@ -786,7 +901,6 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
     }
     to_mma();
-    bool x_in_tmem = false;
     for (int k = 0; k < 6; ++k) {
         if (tid == 0) {
             tc_fence_after();
@@ -810,7 +924,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             if (row < NP) store8(Zh, Zl, row, col0 + 8 * q8, NP, rv, true);   // Z's operand is not needed
         }
         r2 = block_sum(ctl, r2);
-        if (sqrtf(r2) < 1e-6f * (float)P) break;
+        if (k > 0 && sqrtf(r2) < 1e-6f * (float)P) break;
         const bool last = r2 < 1e-6f * (float)P;     // the update lands ||R||_F under the bound
         to_mma();
         if (tid == 0) {
@@ -819,7 +933,6 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             mma_commit(&ctl->bar_mma);
         }
         if (!mma_wait()) return false;
-        x_in_tmem = true;
         if (last) break;                            // X stays in tensor memory
 #pragma unroll 1
         for (int q8 = 0; q8 < nq; ++q8) {
@@ -855,15 +968,29 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         mma_commit(&ctl->bar_mma);
     }
     // own rows: member mean and the mean update X'_E w_bar (compensated sums), under the product
-    for (int e = warp; e < n_e; e += FT / 32) {
+    for (int e = warp; e < n_e; e += FT / 32) {     // four members per lane and load
         const int r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
-        const float* x = A.X + (size_t)r * A.m_pad;
+        const float4* x4 = reinterpret_cast<const float4*>(A.X + (size_t)r * A.m_pad);
+        float4 v[2];
         float sm_ = 0.f;
-        for (int i = lane; i < m; i += 32) sm_ += x[i];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int q = lane + 32 * u;
+            v[u] = q < nq4 ? x4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * q + 0 >= m) v[u].x = 0.f;
+            if (4 * q + 1 >= m) v[u].y = 0.f;
+            if (4 * q + 2 >= m) v[u].z = 0.f;
+            if (4 * q + 3 >= m) v[u].w = 0.f;
+            sm_ += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+        }
         sm_ = warp_sum(sm_);
         const float mu = sm_ / (float)m;
         float us = 0.f, uc = 0.f;
-        for (int i = lane; i < m; i += 32) dot2_add(us, uc, x[i] - mu, wbar[i]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = 4 * (lane + 32 * (u >> 2)) + (u & 3);
+            if (i < m) dot2_add(us, uc, f4c(v[u >> 2], u & 3) - mu, wbar[i]);
+        }
         const float u = dot2_warp(us, uc);
         if (lane == 0) {
             xe_mean[e] = mu;
@@ -890,12 +1017,14 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     for (int t = tid; t < RA * (MP >> 3); t += FT) {
         const int e = t % RA, kc = t / RA;
         float v[8];
-        int r = 0;
-        if (e < n_e) r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = kc * 8 + u;
-            v[u] = (e < n_e && k < m) ? A.X[(size_t)r * A.m_pad + k] - xe_mean[e] : 0.f;
+        for (int u = 0; u < 8; ++u) v[u] = 0.f;
+        if (e < n_e) {
+            const int r = e < n_own ? A.tab.own[e0 + e] : A.n_act + A.tab.own[e0 + e - n_own];
+            get8(A.X + (size_t)r * A.m_pad + kc * 8, v, min(8, A.m_pad - kc * 8));
+            const float mu = xe_mean[e];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = kc * 8 + u < m ? v[u] - mu : 0.f;
         }
         store8(A1h, A1l, e, kc * 8, MP, v, A.tr_terms > 1);
     }
@@ -911,17 +1040,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {
         float xv[8];
-        if (x_in_tmem) {
-            tmem_ld8(tl + TM_G + 8 * q8, xv);
-        } else {                                    // X_1 = 4/3 I - 4/9 (I + Z)
-            float zv[8];
-            zrow(q8, zv);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float id = (row == col0 + 8 * q8 + u) ? 1.f : 0.f;
-                xv[u] = (4.f / 3.f) * id - (4.f / 9.f) * (id + zv[u] * rs);
-            }
-        }
+        tmem_ld8(tl + TM_G + 8 * q8, xv);
 #pragma unroll
         for (int u = 0; u < 8; ++u) xv[u] = (row < P && col0 + 8 * q8 + u < P) ? xv[u] : 0.f;
         if (row < NP) store8(Xh_op, Xl_op, row, col0 + 8 * q8, NP, xv, true);
@@ -1004,33 +1123,58 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     }
     const bool writes = mine && !(ar2 && row >= n_own);
     float psum = 0.f;
-#pragma unroll 1
-    for (int q8 = 0; q8 < mq; ++q8) {
-        float dv[8];
-        tmem_ld8(tlm + TM_Y + 8 * q8, dv);
-        if (!writes) continue;
+    // eight members per chunk, 16-byte loads and stores; the next chunk's state and noise rows are
+    // in flight while this one is written
+    auto eload = [&](int q8, float (&xv)[8], float (&vv)[8]) {
+        const int j0 = mcol0 + 8 * q8, valid = min(8, m - j0);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int j = mcol0 + 8 * q8 + u;
-            if (j < m) {
-                const float xa = A.X[(size_t)grow * A.m_pad + j] + shift - (dv[u] - p3mean);
-                if (A.with_forecast) {
-                    float v = 0.f;
-                    if (A.vmode == 0) {
-                        v = A.V[(size_t)jact * A.m_pad + j];
-                    } else if (A.vmode == 1) {
+        for (int u = 0; u < 8; ++u) xv[u] = vv[u] = 0.f;
+        if (!writes || valid <= 0) return;
+        get8(A.X + (size_t)grow * A.m_pad + j0, xv, valid);
+        if (A.with_forecast && A.vmode == 0) get8(A.V + (size_t)jact * A.m_pad + j0, vv, valid);
+    };
+    {
+        float xc[8], vc[8], xn[8], vn[8];
+        eload(0, xc, vc);
+#pragma unroll 1
+        for (int q8 = 0; q8 < mq; ++q8) {
+            if (q8 + 1 < mq) eload(q8 + 1, xn, vn);
+            float dv[8];
+            tmem_ld8(tlm + TM_Y + 8 * q8, dv);
+            const int j0 = mcol0 + 8 * q8, valid = min(8, m - j0);
+            if (writes && valid > 0) {
+                if (A.with_forecast && A.vmode == 1)
+#pragma unroll 1
+                    for (int u = 0; u < valid; ++u) {
                         float zz[4];
-                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
-                        v = A.q_white * zz[jact & 3];
+                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)(j0 + u), (uint32_t)(jact >> 2), zz);
+                        const float w = A.q_white * zz[jact & 3];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            if (k == u) vc[k] = w;
                     }
-                    const float n1 = A.a * xa + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + v;
-                    A.Xo[(size_t)jact * A.m_pad + j] = n1;
-                    A.Xo[(size_t)(A.n_act + jact) * A.m_pad + j] = xa;
-                    psum += n1;
+                float xa[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xa[u] = xc[u] + shift - (dv[u] - p3mean);
+                if (A.with_forecast) {
+                    float n1[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        n1[u] = A.a * xa[u] + (ar2 && u < valid ? A.a2 * x2buf[row * A.m_pad + j0 + u] : 0.f) + vc[u];
+                        if (u < valid) psum += n1[u];
+                    }
+                    put8(A.Xo + (size_t)jact * A.m_pad + j0, n1, valid);
+                    put8(A.Xo + (size_t)(A.n_act + jact) * A.m_pad + j0, xa, valid);
                 } else {
-                    A.Xo[(size_t)grow * A.m_pad + j] = xa;
+                    put8(A.Xo + (size_t)grow * A.m_pad + j0, xa, valid);
                 }
             }
+            if (q8 + 1 < mq)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    xc[u] = xn[u];
+                    vc[u] = vn[u];
+                }
         }
     }
     if (A.with_forecast) {

@@ -5,7 +5,8 @@ m x m symmetric square root:
 
   w_bar = [(m-1)I + S^T S]^-1 S^T d = S^T (cI + K)^-1 d,               K = S S^T, c = m - 1
   T = (I + S^T S / c)^(-1/2) = I - W^T (I + Z)^-1 W,  Z = (I + K/c)^(-1/2),  W = Z S / sqrt(c)
-  (I + Z)^-1 by Newton's iteration X <- X (2I - (I + Z) X) from 2/3 I: four steps to 1e-8.
+  (I + Z)^-1 by Newton's iteration X <- X (2I - (I + Z) X) from 2/3 I: four steps to 1e-8 (the
+  kernel takes the first step elementwise and predicts the last from the residual's square).
 """
 
 import numpy as np
@@ -58,3 +59,38 @@ def test_newton_inverse_start_contracts_for_every_z_in_the_unit_interval():
     for _ in range(4):
         e = e * e
     assert e.max() < 3e-8
+
+
+@pytest.mark.parametrize("p,seed", [(16, 1), (64, 2), (128, 3)])
+def test_newton_inverse_elementwise_start_and_predicted_last_update(p, seed):
+    # The kernel's schedule for (I + Z)^-1: X_1 = X_0 (2I - M X_0) with X_0 = 2/3 I is the
+    # elementwise 4/3 I - 4/9 M; R_k = I - M X_k squares at every update (X_k is a polynomial in M),
+    # so ||R_{k+1}||_F <= ||R_k||_F^2 and an update taken when ||R_k||_F^2 is under the bound is the
+    # last; at least one update runs.
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    z = rng.uniform(0.02, 1.0, p)                    # eigenvalues of Z in (0, 1]
+    Z = (Q * z) @ Q.T
+    M = np.eye(p) + Z
+    X0 = (2.0 / 3.0) * np.eye(p)
+    X = (4.0 / 3.0) * np.eye(p) - (4.0 / 9.0) * M
+    np.testing.assert_allclose(X, X0 @ (2.0 * np.eye(p) - M @ X0), rtol=0, atol=1e-15)
+    tol = 1e-6 * p
+    updates = 0
+    for k in range(6):
+        R = np.eye(p) - M @ X
+        r2 = float(np.sum(R * R))
+        if k > 0 and np.sqrt(r2) < tol:
+            break
+        last = r2 < tol
+        Xn = X @ (2.0 * np.eye(p) - M @ X)
+        Rn = np.eye(p) - M @ Xn
+        np.testing.assert_allclose(Rn, R @ R, rtol=0, atol=1e-12)
+        assert np.linalg.norm(Rn) <= r2 * (1 + 1e-12) + 1e-14
+        X = Xn
+        updates += 1
+        if last:
+            break
+    assert 1 <= updates <= 4
+    assert np.linalg.norm(np.eye(p) - M @ X) < tol
+    np.testing.assert_allclose(X, np.linalg.inv(M), rtol=0, atol=1e-6)
