@@ -512,6 +512,52 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         tc_fence_before();
         __syncthreads();
     };
+    // the block sum of v and the operands written by the threads made visible to the tensor core,
+    // in one barrier (ctl->red is read after it: a barrier must come before its next write)
+    auto sum_to_mma = [&](float v) -> float {
+        v = warp_sum(v);
+        if (lane == 0) ctl->red[warp] = v;
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < FT / 32; ++w) t += ctl->red[w];
+        return t;
+    };
+    // Y T (unless with_y is false) and T Z, committed together
+    auto yt_tz = [&](unsigned char* Yh_, unsigned char* Yl_, unsigned char* Th_, unsigned char* Tl_,
+                     unsigned char* Zh_, unsigned char* Zl_, bool with_y) -> bool {
+        if (tid == 0) {
+            tc_fence_after();
+            if (with_y) issue_product(tbase + TM_Y, Yh_, Yl_, Th_, Tl_, NP, NP, 3, 1);
+            issue_product(tbase + TM_Z, Th_, Tl_, Zh_, Zl_, NP, NP, 3, 1);
+            mma_commit(&ctl->bar_mma);
+        }
+        if (!wait_all(ctl, &ctl->bar_mma, ph_mma, A.status)) return false;
+        ph_mma ^= 1;
+        tc_fence_after();
+        return true;
+    };
+    auto read_yz = [&]() {    // Y and Z from tensor memory into their operands, two loads in flight
+#pragma unroll 1
+        for (int q8 = 0; q8 < nq; ++q8) {
+            uint32_t ry[8], rz[8];
+            tmem_ld8_async(tl + TM_Y + 8 * q8, ry);
+            tmem_ld8_async(tl + TM_Z + 8 * q8, rz);
+            tmem_wait_ld(ry, rz);
+            float yv[8], zv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                yv[u] = __uint_as_float(ry[u]);
+                zv[u] = __uint_as_float(rz[u]);
+            }
+            if (row < NP) {
+                store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
+                store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
+            }
+        }
+    };
 
     // ---- halo anomalies of the observed instant (FP32) into the scratch: sixteen lanes per row and
     //      four members per load, 16 rows per pass; the padding columns m .. m_pad are written as 0
@@ -660,27 +706,12 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     if (rn_prev >= 2e-6f * (float)P) {   // else converged at once: Z = I
         to_mma();
         const bool last0 = rn_prev < ns_last;
-        if (tid == 0) {
-            tc_fence_after();
-            if (!last0) issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y_1 = Y_0 T_0
-            issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);                 // Z_1 = T_0
-            mma_commit(&ctl->bar_mma);
-        }
-        if (!mma_wait()) return false;
+        if (!yt_tz(Yh, Yl, Th, Tl, Zh, Zl, !last0)) return false;    // Y_1 = Y_0 T_0, Z_1 = T_0 Z_0
         z_in_tmem = true;
         if (!last0) {                    // else the update was the last: Z_1 = T_0
             it = 1;
             more = true;
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                float yv[8], zv[8];
-                tmem_ld8(tl + TM_Y + 8 * q8, yv);
-                tmem_ld8(tl + TM_Z + 8 * q8, zv);
-                if (row < NP) {
-                    store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                    store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
-                }
-            }
+            read_yz();
             to_mma();
         }
     }
@@ -693,10 +724,8 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         }
         if (!mma_wait()) return false;
         float r2 = 0.f;
-#pragma unroll 1
-        for (int q8 = 0; q8 < nq; ++q8) {
-            float pv[8], tv[8];
-            tmem_ld8(tl + TM_P + 8 * q8, pv);
+        tmem_rows(tl + TM_P, nq, [&](int q8, const float (&pv)[8]) {
+            float tv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int j = col0 + 8 * q8 + u;
@@ -707,41 +736,18 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
                 tv[u] = in ? 1.5f * id - 0.5f * pv[u] : 0.f;
             }
             if (row < NP) store8(Th, Tl, row, col0 + 8 * q8, NP, tv, true);
-        }
-        r2 = block_sum(ctl, r2);
+        });
+        r2 = sum_to_mma(r2);              // one barrier: the residual and T to the tensor core
         const float rn = sqrtf(r2);
         const bool conv = rn < 2e-6f * (float)P || (rn < 2e-2f && rn > 0.6f * rn_prev);
         rn_prev = rn;
         if (conv) break;
-        to_mma();
-        if (rn < ns_last) {    // the last update (see the m x m form): only T Z is used afterwards
-            if (tid == 0) {
-                tc_fence_after();
-                issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
-                mma_commit(&ctl->bar_mma);
-            }
-            if (!mma_wait()) return false;
-            z_in_tmem = true;
-            break;
-        }
-        if (tid == 0) {
-            tc_fence_after();
-            issue_product(tbase + TM_Y, Yh, Yl, Th, Tl, NP, NP, 3, 1);     // Y T
-            issue_product(tbase + TM_Z, Th, Tl, Zh, Zl, NP, NP, 3, 1);     // T Z
-            mma_commit(&ctl->bar_mma);
-        }
-        if (!mma_wait()) return false;
-#pragma unroll 1
-        for (int q8 = 0; q8 < nq; ++q8) {
-            float yv[8], zv[8];
-            tmem_ld8(tl + TM_Y + 8 * q8, yv);
-            tmem_ld8(tl + TM_Z + 8 * q8, zv);
-            if (row < NP) {
-                store8(Yh, Yl, row, col0 + 8 * q8, NP, yv, true);
-                store8(Zh, Zl, row, col0 + 8 * q8, NP, zv, true);
-            }
-        }
+        // the last update (see the m x m form): only T Z is used afterwards
+        const bool last = rn < ns_last;
+        if (!yt_tz(Yh, Yl, Th, Tl, Zh, Zl, !last)) return false;
         z_in_tmem = true;
+        if (last) break;
+        read_yz();
         to_mma();
     }
     if (it == A.max_it && tid == 0) atomicOr(A.status, ST_NOCONV);
@@ -877,12 +883,16 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         for (int t = tid; t < m; t += FT) A.cap[CAP_HDR + t] = wbar[t];
     }
     // ---- (I + Z)^-1, Z = Z_ns / sqrt(s), by Newton's iteration X <- X (2I - (I + Z) X) from
-    //      X_0 = 2/3 I (the eigenvalues of I - (I + Z) X_0 lie in [-1/3, 1/3]); X_k in TMEM slot G.
-    //      The first step is elementwise, X_1 = 4/3 I - 4/9 (I + Z); the residual R = I - M X
-    //      squares at every step, so once ||R||_F^2 is under the stopping bound the update is the
-    //      last and the product that would confirm it is skipped.  At least one update runs, so X
-    //      ends in tensor memory.
+    //      X_0 = alpha I; X_k in TMEM slot G.  Z's eigenvalues (1 + l/c)^(-1/2) lie in
+    //      [s_scale^(-1/2), 1] (every eigenvalue l of K is at most ||K||_F), those of M = I + Z in
+    //      [1 + s_scale^(-1/2), 2], so alpha = 2 / (3 + s_scale^(-1/2)) puts the eigenvalues of
+    //      I - M X_0 within +-(1 - s_scale^(-1/2)) / (3 + s_scale^(-1/2)), at most 1/3.  The first
+    //      step is elementwise, X_1 = 2 alpha I - alpha^2 M; the residual R = I - M X squares at
+    //      every step, so once ||R||_F^2 is under the stopping bound the update is the last and the
+    //      product that would confirm it is skipped.  At least one update runs, so X ends in
+    //      tensor memory.
     const float rs = rsqrtf(s_ns);
+    const float alpha = 2.f / (3.f + rsqrtf(s_scale));
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {               // M = I + Z into Y's buffers, X_1 into T's
         float zv[8], mv[8], xv[8];
@@ -893,7 +903,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             const bool in = row < P && j < P;
             const float id = (row == j) ? 1.f : 0.f;
             mv[u] = in ? id + zv[u] * rs : 0.f;
-            xv[u] = in ? (4.f / 3.f) * id - (4.f / 9.f) * mv[u] : 0.f;
+            xv[u] = in ? 2.f * alpha * id - alpha * alpha * mv[u] : 0.f;
         }
         if (row < NP) {
             store8(Yh, Yl, row, col0 + 8 * q8, NP, mv, true);
@@ -1607,8 +1617,8 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                     atomicExch(A.dom_bad, 1);
                     atomicOr(A.status, ST_NONFINITE);
                 }
-            } else if (!analyse_dual(ctl, smem, tbase, &ph_mma, d)) {
-                break;
+            } else {
+                if (!analyse_dual(ctl, smem, tbase, &ph_mma, d)) break;
             }
             __syncthreads();
             if (warp == 0) fetch_item(B, ctl, smem, 1 << 30);

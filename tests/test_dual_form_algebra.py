@@ -64,7 +64,7 @@ def test_newton_inverse_start_contracts_for_every_z_in_the_unit_interval():
 @pytest.mark.parametrize("p,seed", [(16, 1), (64, 2), (128, 3)])
 def test_newton_inverse_elementwise_start_and_predicted_last_update(p, seed):
     # The kernel's schedule for (I + Z)^-1: X_1 = X_0 (2I - M X_0) with X_0 = 2/3 I is the
-    # elementwise 4/3 I - 4/9 M; R_k = I - M X_k squares at every update (X_k is a polynomial in M),
+    # elementwise 4/3 I - 4/9 M (with X_0 = alpha I, 2 alpha I - alpha^2 M); R_k = I - M X_k squares at every update (X_k is a polynomial in M),
     # so ||R_{k+1}||_F <= ||R_k||_F^2 and an update taken when ||R_k||_F^2 is under the bound is the
     # last; at least one update runs.
     rng = np.random.default_rng(seed)
@@ -75,6 +75,17 @@ def test_newton_inverse_elementwise_start_and_predicted_last_update(p, seed):
     X0 = (2.0 / 3.0) * np.eye(p)
     X = (4.0 / 3.0) * np.eye(p) - (4.0 / 9.0) * M
     np.testing.assert_allclose(X, X0 @ (2.0 * np.eye(p) - M @ X0), rtol=0, atol=1e-15)
+    # the kernel's start alpha I, alpha = 2 / (3 + s^(-1/2)), s = 1 + ||K||_F / c, contracts at least
+    # as fast as 2/3 I: here K = c (Z^-2 - I), so s^(-1/2) is a lower bound on Z's spectrum
+    c = 99.0
+    K = c * (np.linalg.inv(Z @ Z) - np.eye(p))
+    s_scale = 1.0 + np.linalg.norm(K) / c
+    assert z.min() >= s_scale ** -0.5 * (1 - 1e-12)
+    alpha = 2.0 / (3.0 + s_scale ** -0.5)
+    rho = np.abs(1.0 - alpha * (1.0 + z)).max()
+    assert rho <= (1.0 - s_scale ** -0.5) / (3.0 + s_scale ** -0.5) + 1e-12 <= 1.0 / 3.0 + 1e-12
+    X = 2.0 * alpha * np.eye(p) - alpha * alpha * M
+    np.testing.assert_allclose(X, alpha * (2.0 * np.eye(p) - alpha * M), rtol=0, atol=1e-15)
     tol = 1e-6 * p
     updates = 0
     for k in range(6):
