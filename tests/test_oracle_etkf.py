@@ -288,3 +288,21 @@ def test_initial_ensemble_is_a_stationary_ar1_pair():
     C = np.cov(X[g.n_act:])
     S = L_stat @ L_stat.T
     assert np.abs(C - S).max() < 6 * np.sqrt(2.0 / m) * np.abs(S).max()
+
+
+def test_process_covariance_is_the_covariance_of_the_forecast_noise():
+    # Q of the two-instant state is the second moment of what the forecast adds to a member beyond
+    # A1 x: with V = L xi and xi running over the unit vectors (m = n_act members, E[xi xi^T] = I
+    # in the sample sense), the added columns D = f(X, V) - f(X, 0) give D D^T = Q exactly.  A
+    # transposed factor (L^T L) or the noise on the wrong instant fails this.
+    rng = np.random.default_rng(7)
+    n_act = 9
+    L = np.tril(rng.standard_normal((n_act, n_act)))
+    X = rng.standard_normal((2 * n_act, n_act))
+    D = etkf.forecast(X, 0.9, L @ np.eye(n_act)) - etkf.forecast(X, 0.9, np.zeros((n_act, n_act)))
+    Q = kf.process_covariance(L)
+    np.testing.assert_allclose(D @ D.T, Q, rtol=0, atol=1e-12)
+    assert np.abs(Q[n_act:]).max() == 0.0 and np.abs(Q[:, n_act:]).max() == 0.0
+    assert not np.allclose(Q[:n_act, :n_act], L.T @ L)
+    # and A1 X + D is the forecast (the deterministic part is the companion matrix)
+    np.testing.assert_allclose(etkf.forecast(X, 0.9, L) - D, kf.ar1_companion(n_act, 0.9) @ X, rtol=0, atol=1e-12)
