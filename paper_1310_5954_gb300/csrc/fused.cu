@@ -2154,11 +2154,6 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             }
         };
         const bool mine = row < n_e;
-        int grow = 0, jact = 0;
-        if (mine) {
-            jact = row < n_own ? owns[row] : owns[row - n_own];
-            grow = row < n_own ? jact : A.n_act + jact;
-        }
         // the tensor-core product is read from tensor memory once: its rows go to shared memory
         // (FP32, row stride NP + 4, over Z's rows, which the transform no longer needs) for the
         // passes below
@@ -2213,79 +2208,73 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             }
             __syncthreads();
         }
-        const bool writes = mine && !(ar2 && row >= n_own);
-        const bool dense_v = writes && A.with_forecast && A.vmode == 0;
-        float psum = 0.f;
-        // analysis rows, forecast and prediction sum for 8 columns: dv of X'_E T, vc of the noise
-        auto put = [&](int q8, const float (&dv)[8], const float (&vc)[8]) {
-            if (!writes) return;
-            const int c8 = col0 + 8 * q8, valid = m - c8;
-            if (valid <= 0) return;
-            float xa[8], n1[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = c8 + u;
-                xa[u] = shift + dv[u];
-                if (A.with_forecast && j < m) {
-                    n1[u] = A.a * xa[u] + (ar2 ? A.a2 * x2buf[row * A.m_pad + j] : 0.f) + vc[u];
-                    psum += n1[u];
-                } else {
-                    n1[u] = 0.f;
-                }
-            }
-            if (A.with_forecast) {
-                put8(A.Xo + (size_t)jact * A.m_pad + c8, n1, valid);
-                put8(A.Xo + (size_t)(A.n_act + jact) * A.m_pad + c8, xa, valid);
-            } else {
-                put8(A.Xo + (size_t)grow * A.m_pad + c8, xa, valid);
-            }
-        };
-        const float* vrow = vsm ? reinterpret_cast<const float*>(big + A.off_vs) +
-                                      (size_t)(row < n_own ? row : row - n_own) * A.m_pad + col0
-                                : A.V + (size_t)jact * A.m_pad + col0;
-        // the process noise of 8 columns: V's rows, or white noise drawn here (kept out of the
-        // unrolled arithmetic above: its Philox code inlined there cost instruction-cache misses)
-        const bool white_v = writes && A.with_forecast && A.vmode == 1;
-        auto vload = [&](int q8, float (&v)[8]) {
-            if (dense_v) {
-                get8(vrow + 8 * q8, v, m - col0 - 8 * q8);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = 0.f;
-                if (white_v)
+        // analysis rows, forecast and prediction: sixteen lanes per row, a chunk of 8 members each
+        // (the rows are few: one thread per row and column half left most threads idle, and made
+        // each store a different row's); the row's prediction sum by a shuffle tree
+        {
+            const int nck = (m + 7) >> 3;           // chunks of a row (<= 16)
+            const int l16 = lane & 15;
+            const float* vbase = vsm ? reinterpret_cast<const float*>(big + A.off_vs) : A.V;
 #pragma unroll 1
-                    for (int u = 0; u < 8; ++u) {
-                        const int j = col0 + 8 * q8 + u;
-                        if (j < m) {
+            for (int r0 = 2 * warp; r0 < n_e; r0 += FT / 16) {
+                const int e = r0 + (lane >> 4);
+                const bool row_w = e < n_e && !(ar2 && e >= n_own);
+                const bool wr = row_w && l16 < nck;
+                int ja = 0;
+                if (e < n_e) ja = e < n_own ? owns[e] : owns[e - n_own];
+                float n1s = 0.f;
+                if (wr) {
+                    const int c8 = 8 * l16, valid = min(8, m - c8);
+                    const float sh = xe_mean[e] + uvec[e] - (vtmp[e] + vtmp[128 + e]) / (float)m;
+                    float dv[8], vc[8];
+                    if (simt) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) dv[u] = c8 + u < m ? sout[e * sld + c8 + u] : 0.f;
+                    } else {
+                        const float4* src = reinterpret_cast<const float4*>(pst + e * pld + c8);
+                        const float4 p0 = src[0], p1 = src[1];
+                        dv[0] = p0.x; dv[1] = p0.y; dv[2] = p0.z; dv[3] = p0.w;
+                        dv[4] = p1.x; dv[5] = p1.y; dv[6] = p1.z; dv[7] = p1.w;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) vc[u] = 0.f;
+                    if (A.with_forecast && A.vmode == 0) {
+                        const int ev = vsm ? (e < n_own ? e : e - n_own) : ja;
+                        get8(vbase + (size_t)ev * A.m_pad + c8, vc, valid);
+                    } else if (A.with_forecast && A.vmode == 1) {
+                        // white noise drawn here (kept out of the unrolled arithmetic below: its
+                        // Philox code inlined there cost instruction-cache misses)
+#pragma unroll 1
+                        for (int u = 0; u < valid; ++u) {
                             float zz[4];
-                            normals4<float>(A.seed, 1u, A.frame, (uint32_t)j, (uint32_t)(jact >> 2), zz);
-                            const float w = A.q_white * zz[jact & 3];
+                            normals4<float>(A.seed, 1u, A.frame, (uint32_t)(c8 + u), (uint32_t)(ja >> 2), zz);
+                            const float w = A.q_white * zz[ja & 3];
                             // a register array indexed by a runtime u would live in local memory
 #pragma unroll
                             for (int k = 0; k < 8; ++k)
-                                if (k == u) v[k] = w;
+                                if (k == u) vc[k] = w;
                         }
                     }
-            }
-        };
-        {   // the next chunk's noise loads are in flight while this one is written
-            float vc[8], vn[8];
-            vload(0, vc);
-#pragma unroll 1
-            for (int q8 = 0; q8 < nq; ++q8) {
-                if (q8 + 1 < nq) vload(q8 + 1, vn);
-                float dv[8];
-                srow(q8, dv);
-                put(q8, dv, vc);
-                if (q8 + 1 < nq)
+                    float xa[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) vc[u] = vn[u];
+                    for (int u = 0; u < 8; ++u) xa[u] = sh + dv[u];
+                    if (A.with_forecast) {
+                        float n1[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            n1[u] = u < valid ? A.a * xa[u] + (ar2 ? A.a2 * x2buf[e * A.m_pad + c8 + u] : 0.f) + vc[u] : 0.f;
+                            n1s += n1[u];
+                        }
+                        put8(A.Xo + (size_t)ja * A.m_pad + c8, n1, valid);
+                        put8(A.Xo + (size_t)(A.n_act + ja) * A.m_pad + c8, xa, valid);
+                    } else {
+                        put8(A.Xo + (size_t)(e < n_own ? ja : A.n_act + ja) * A.m_pad + c8, xa, valid);
+                    }
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) n1s += __shfl_xor_sync(0xffffffffu, n1s, o);
+                if (A.with_forecast && A.xpred && row_w && l16 == 0) A.xpred[ja] = n1s / (float)m;
             }
-        }
-        if (A.with_forecast) {
-            vtmp[hh * 128 + row] = psum;
-            __syncthreads();
-            if (hh == 0 && writes && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
         }
         tc_fence_before();
         __syncthreads();
