@@ -88,7 +88,8 @@ struct SysDesc {
     // shared-memory layout (bytes from the dynamic base); vec and XE start at the same offset
     // for every system, so a region below off_big never overlaps another system's operands
     int off_vec, off_xe, off_xh, off_big, sz_op, sz_opg, sz_a;
-    int off_zf;          // m x m form: FP32 rows of Z in the big region, past the transform's operands
+    int off_zf;          // m x m form: FP32 rows of Z in the big region, past the transform's operands;
+                         // dual form: FP32 rows of the transform product P3 for the epilogue
     int off_vs;          // m x m form: the domain's rows of the process noise V (in the big region), or -1
     // test instrument: when cap is set, the analysis of domain cap_dom writes what it computed
     // (header, mean weights, transform or its factors; layout in letkf_set_capture) to cap
@@ -1091,106 +1092,93 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         mma_commit(&ctl->bar_mma);
     }
     if (!mma_wait()) return false;
-    // ---- epilogue: X_a = X + X'_E w_bar - (P3 - row mean of P3); forecast; prediction
+    // ---- epilogue: X_a = X + X'_E w_bar - (P3 - row mean of P3); forecast; prediction.  P3 is
+    //      read from tensor memory once (row sums, and its rows to shared memory); then a warp per
+    //      own row, a chunk of 8 members per lane (one thread per row and column half left most
+    //      threads idle, and made each store a different row's)
     const bool mine = row < n_e;
-    int grow = 0, jact = 0;
-    if (mine) {
-        jact = row < n_own ? A.tab.own[e0 + row] : A.tab.own[e0 + row - n_own];
-        grow = row < n_own ? jact : A.n_act + jact;
-    }
+    float* p3s = reinterpret_cast<float*>(big + A.off_zf);
+    const int pld = MP + 4;
     {
         float part = 0.f;
-#pragma unroll 1
-        for (int q8 = 0; q8 < mq; ++q8) {
-            float dv[8];
-            tmem_ld8(tlm + TM_Y + 8 * q8, dv);
+        tmem_rows(tlm + TM_Y, mq, [&](int q8, const float (&dv)[8]) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
                 if (mcol0 + 8 * q8 + u < m) part += dv[u];
-        }
+            if (mine) {
+                float4* dst = reinterpret_cast<float4*>(p3s + row * pld + mcol0 + 8 * q8);
+                dst[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                dst[1] = make_float4(dv[4], dv[5], dv[6], dv[7]);
+            }
+        });
         vtmp[hh * 128 + row] = part;
         __syncthreads();
     }
-    const float p3mean = mine ? (vtmp[row] + vtmp[128 + row]) / (float)m : 0.f;
-    const float shift = mine ? uvec[row] : 0.f;
-    __syncthreads();
     // AR(2) forecast: second-instant rows hand their analysis to the first-instant rows
     const bool ar2 = A.with_forecast && A.a2 != 0.f;
     float* x2buf = reinterpret_cast<float*>(big);
     if (ar2) {
-#pragma unroll 1
-        for (int q8 = 0; q8 < mq; ++q8) {
-            float dv[8];
-            tmem_ld8(tlm + TM_Y + 8 * q8, dv);
-            if (mine && row >= n_own)
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = mcol0 + 8 * q8 + u;
-                    if (j < m) x2buf[(row - n_own) * A.m_pad + j] = A.X[(size_t)grow * A.m_pad + j] + shift - (dv[u] - p3mean);
-                }
+        for (int t = tid; t < (n_e - n_own) * m; t += FT) {
+            const int r = n_own + t / m, j = t - (t / m) * m;
+            const int ja = A.tab.own[e0 + r - n_own];
+            const float p3mean = (vtmp[r] + vtmp[128 + r]) / (float)m;
+            x2buf[(r - n_own) * A.m_pad + j] =
+                A.X[(size_t)(A.n_act + ja) * A.m_pad + j] + uvec[r] - (p3s[r * pld + j] - p3mean);
         }
         __syncthreads();
     }
-    const bool writes = mine && !(ar2 && row >= n_own);
-    float psum = 0.f;
-    // eight members per chunk, 16-byte loads and stores; the next chunk's state and noise rows are
-    // in flight while this one is written
-    auto eload = [&](int q8, float (&xv)[8], float (&vv)[8]) {
-        const int j0 = mcol0 + 8 * q8, valid = min(8, m - j0);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) xv[u] = vv[u] = 0.f;
-        if (!writes || valid <= 0) return;
-        get8(A.X + (size_t)grow * A.m_pad + j0, xv, valid);
-        if (A.with_forecast && A.vmode == 0) get8(A.V + (size_t)jact * A.m_pad + j0, vv, valid);
-    };
-    {
-        float xc[8], vc[8], xn[8], vn[8];
-        eload(0, xc, vc);
+    const int nck = (m + 7) >> 3;                    // chunks of a row (<= 32)
 #pragma unroll 1
-        for (int q8 = 0; q8 < mq; ++q8) {
-            if (q8 + 1 < mq) eload(q8 + 1, xn, vn);
-            float dv[8];
-            tmem_ld8(tlm + TM_Y + 8 * q8, dv);
-            const int j0 = mcol0 + 8 * q8, valid = min(8, m - j0);
-            if (writes && valid > 0) {
-                if (A.with_forecast && A.vmode == 1)
+    for (int e = warp; e < n_e; e += FT / 32) {
+        const bool row_w = !(ar2 && e >= n_own);
+        const int ja = e < n_own ? A.tab.own[e0 + e] : A.tab.own[e0 + e - n_own];
+        const int gr = e < n_own ? ja : A.n_act + ja;
+        const float p3mean = (vtmp[e] + vtmp[128 + e]) / (float)m;
+        const float shift = uvec[e];
+        float n1s = 0.f;
+        for (int ck = lane; ck < nck && row_w; ck += 32) {
+            const int c8 = 8 * ck, valid = min(8, m - c8);
+            float dv[8], xv[8], vc[8];
+            {
+                const float4* src = reinterpret_cast<const float4*>(p3s + e * pld + c8);
+                const float4 p0 = src[0], p1 = src[1];
+                dv[0] = p0.x; dv[1] = p0.y; dv[2] = p0.z; dv[3] = p0.w;
+                dv[4] = p1.x; dv[5] = p1.y; dv[6] = p1.z; dv[7] = p1.w;
+            }
+            get8(A.X + (size_t)gr * A.m_pad + c8, xv, valid);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) vc[u] = 0.f;
+            if (A.with_forecast && A.vmode == 0) {
+                get8(A.V + (size_t)ja * A.m_pad + c8, vc, valid);
+            } else if (A.with_forecast && A.vmode == 1) {
 #pragma unroll 1
-                    for (int u = 0; u < valid; ++u) {
-                        float zz[4];
-                        normals4<float>(A.seed, 1u, A.frame, (uint32_t)(j0 + u), (uint32_t)(jact >> 2), zz);
-                        const float w = A.q_white * zz[jact & 3];
+                for (int u = 0; u < valid; ++u) {
+                    float zz[4];
+                    normals4<float>(A.seed, 1u, A.frame, (uint32_t)(c8 + u), (uint32_t)(ja >> 2), zz);
+                    const float w = A.q_white * zz[ja & 3];
 #pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            if (k == u) vc[k] = w;
-                    }
-                float xa[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) xa[u] = xc[u] + shift - (dv[u] - p3mean);
-                if (A.with_forecast) {
-                    float n1[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        n1[u] = A.a * xa[u] + (ar2 && u < valid ? A.a2 * x2buf[row * A.m_pad + j0 + u] : 0.f) + vc[u];
-                        if (u < valid) psum += n1[u];
-                    }
-                    put8(A.Xo + (size_t)jact * A.m_pad + j0, n1, valid);
-                    put8(A.Xo + (size_t)(A.n_act + jact) * A.m_pad + j0, xa, valid);
-                } else {
-                    put8(A.Xo + (size_t)grow * A.m_pad + j0, xa, valid);
+                    for (int k = 0; k < 8; ++k)
+                        if (k == u) vc[k] = w;
                 }
             }
-            if (q8 + 1 < mq)
+            float xa[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xa[u] = xv[u] + shift - (dv[u] - p3mean);
+            if (A.with_forecast) {
+                float n1[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    xc[u] = xn[u];
-                    vc[u] = vn[u];
+                    n1[u] = u < valid ? A.a * xa[u] + (ar2 ? A.a2 * x2buf[e * A.m_pad + c8 + u] : 0.f) + vc[u] : 0.f;
+                    n1s += n1[u];
                 }
+                put8(A.Xo + (size_t)ja * A.m_pad + c8, n1, valid);
+                put8(A.Xo + (size_t)(A.n_act + ja) * A.m_pad + c8, xa, valid);
+            } else {
+                put8(A.Xo + (size_t)gr * A.m_pad + c8, xa, valid);
+            }
         }
-    }
-    if (A.with_forecast) {
-        vtmp[hh * 128 + row] = psum;
-        __syncthreads();
-        if (hh == 0 && writes && A.xpred) A.xpred[jact] = (vtmp[row] + vtmp[128 + row]) / (float)m;
+        n1s = warp_sum(n1s);
+        if (A.with_forecast && A.xpred && row_w && lane == 0) A.xpred[ja] = n1s / (float)m;
     }
     tc_fence_before();
     __syncthreads();
@@ -2415,7 +2403,11 @@ FusedLayout fused_layout(const letkf_ctx* c) {
         const int ns = std::max(6 * L.sz_op, 5 * L.sz_op + MT * L.NP * 2);
         const int tr = std::max(std::max(L.sz_a + 2 * L.sz_opg, L.RA * L.KP * 2 + MT * L.KP * 2),
                                 std::max(L.sz_op + MT * L.NP * 2, L.RA * L.NP * 2 + MT * L.NP * 2));
-        L.total = L.off_big + round_up(std::max(gram, std::max(ns, tr)), 1024);
+        // the epilogue's FP32 rows of P3 (RA x KP, row stride KP + 4) over the transform's p x m
+        // operands, which are read by then; below them the AR(2) hand-over rows
+        L.off_zf = L.sz_a;
+        const int epi = L.off_zf + L.RA * (L.KP + 4) * 4;
+        L.total = L.off_big + round_up(std::max(std::max(gram, epi), std::max(ns, tr)), 1024);
         return L;
     }
     L.NP = round_up(c->m + 1, 16);
