@@ -763,15 +763,34 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             for (int u = 0; u < 8; ++u) zv[u] = (row == col0 + 8 * q8 + u && row < P) ? 1.f : 0.f;
         }
     };
+    // Z_ns's rows in FP32 in the big region for the mean weights (free between the iterations);
+    // each thread writes and reads only its own half-row
+    float* zf = reinterpret_cast<float*>(big + 8192);
+    const int zld = NP + 4;
+#pragma unroll 1
+    for (int q8 = 0; q8 < nq; ++q8) {
+        float zv[8];
+        zrow(q8, zv);
+        if (row < NP) {
+            float4* d4 = reinterpret_cast<float4*>(zf + row * zld + col0 + 8 * q8);
+            d4[0] = make_float4(zv[0], zv[1], zv[2], zv[3]);
+            d4[1] = make_float4(zv[4], zv[5], zv[6], zv[7]);
+        }
+    }
     auto zmatvec = [&](const float* x_in, float* y_out) {   // y = Z_ns x over the first P entries
         float part = 0.f;
-#pragma unroll 1
-        for (int q8 = 0; q8 < nq; ++q8) {
-            float zv[8];
-            zrow(q8, zv);
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (col0 + 8 * q8 + u < P) part += zv[u] * x_in[col0 + 8 * q8 + u];
+        if (row < NP) {
+            const float4* z4 = reinterpret_cast<const float4*>(zf + row * zld + col0);
+            const float4* x4 = reinterpret_cast<const float4*>(x_in + col0);
+#pragma unroll 2
+            for (int q = 0; q < 2 * nq; ++q) {
+                const float4 z = z4[q], x = x4[q];
+                const int j = col0 + 4 * q;
+                if (j + 0 < P) part += z.x * x.x;
+                if (j + 1 < P) part += z.y * x.y;
+                if (j + 2 < P) part += z.z * x.z;
+                if (j + 3 < P) part += z.w * x.w;
+            }
         }
         vtmp[hh * 128 + row] = part;
         __syncthreads();
