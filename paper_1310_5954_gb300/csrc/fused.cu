@@ -91,6 +91,9 @@ struct SysDesc {
     int off_zf;          // m x m form: FP32 rows of Z in the big region, past the transform's operands;
                          // dual form: FP32 rows of the transform product P3 for the epilogue
     int off_vs;          // m x m form: the domain's rows of the process noise V (in the big region), or -1
+    int off_hs;          // dual form: the halo anomalies' rows in the big region beside the Gram operand, or -1
+    int off_hs2;         // dual form: the same rows beside Z's FP32 rows for the mean weights, or -1
+    int hs_w;            // dual form: the same rows fit below the W operand (at the big region's start)
     // test instrument: when cap is set, the analysis of domain cap_dom writes what it computed
     // (header, mean weights, transform or its factors; layout in letkf_set_capture) to cap
     float* cap;
@@ -565,6 +568,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const int nq4 = A.m_pad >> 2;                   // <= 64
     const int g8 = lane >> 3, l8 = lane & 7;
     float4* Xs4 = reinterpret_cast<float4*>(Xs);
+    float4* Hs4 = A.off_hs >= 0 ? reinterpret_cast<float4*>(big + A.off_hs) : nullptr;   // copy in shared memory
     for (int j0 = 2 * warp; j0 < n_h; j0 += FT / 16) {
         const int j = j0 + (lane >> 4), l16 = lane & 15;
         const bool has = j < n_h;
@@ -588,9 +592,12 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int q = l16 + 16 * u;
-                if (q < nq4)
-                    Xs4[(size_t)j * nq4 + q] = make_float4(4 * q + 0 < m ? v[u].x - mu : 0.f, 4 * q + 1 < m ? v[u].y - mu : 0.f,
-                                                           4 * q + 2 < m ? v[u].z - mu : 0.f, 4 * q + 3 < m ? v[u].w - mu : 0.f);
+                if (q < nq4) {
+                    const float4 a4 = make_float4(4 * q + 0 < m ? v[u].x - mu : 0.f, 4 * q + 1 < m ? v[u].y - mu : 0.f,
+                                                  4 * q + 2 < m ? v[u].z - mu : 0.f, 4 * q + 3 < m ? v[u].w - mu : 0.f);
+                    Xs4[(size_t)j * nq4 + q] = a4;
+                    if (Hs4) Hs4[(size_t)j * nq4 + q] = a4;
+                }
             }
             if (l16 == 0) xh_mean[j] = mu;
         }
@@ -610,7 +617,13 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     }
     // S as an NP x MP operand (rows: slopes, K: members): both slopes of a subaperture from one
     //      read of its four corners' anomalies, eight members at a time
-    auto write_S = [&](unsigned char* hi, unsigned char* lo) {
+    auto restage = [&](float4* dst4) {    // the halo anomalies' rows from the scratch (L2) into shared memory
+        for (int t = tid; t < n_h * nq4; t += FT) cp_async16(dst4 + t, Xs4 + t);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+    };
+    auto write_S = [&](unsigned char* hi, unsigned char* lo, const float4* src4) {
         const int ns2 = NP >> 1;
         for (int t = tid; t < ns2 * (MP >> 3); t += FT) {
             const int sb = t % ns2, ic = t / ns2;
@@ -622,7 +635,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
                 float4 c[4][2];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4* r = Xs4 + (size_t)((pc >> (8 * q)) & 0xFF) * nq4 + 2 * ic;
+                    const float4* r = src4 + (size_t)((pc >> (8 * q)) & 0xFF) * nq4 + 2 * ic;
                     c[q][0] = 8 * ic + 4 <= A.m_pad ? r[0] : make_float4(0.f, 0.f, 0.f, 0.f);
                     c[q][1] = 8 * ic + 8 <= A.m_pad ? r[1] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -641,7 +654,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     };
     unsigned char* Sg_h = big;
     unsigned char* Sg_l = big + A.sz_opg;
-    write_S(Sg_h, Sg_l);
+    write_S(Sg_h, Sg_l, Hs4 ? Hs4 : Xs4);
     to_mma();
     if (tid == 0) {
         tc_fence_after();
@@ -797,6 +810,13 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         if (hh == 0) y_out[row] = (row < P) ? vtmp[row] + vtmp[128 + row] : 0.f;
         __syncthreads();
     };
+    // the halo anomalies' rows for the mean weights: in shared memory past Z's rows when they fit
+    const float4* H4m = Xs4;
+    if (A.off_hs2 >= 0) {
+        float4* d4 = reinterpret_cast<float4*>(big + A.off_hs2);
+        restage(d4);
+        H4m = d4;
+    }
     // S = D_loc X'_h / sigma is linear in the halo anomalies: S^T u is X'_h^T applied to the
     // stencil's transpose of u, and S w the stencil of X'_h w (n_h x m products over the scratch
     // instead of four scratch loads per slope and member)
@@ -824,7 +844,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
                 for (int j = ja; j < jb; ++j) {
-                    const float4 x = Xs4[(size_t)j * nq4 + q];
+                    const float4 x = H4m[(size_t)j * nq4 + q];
                     const float h = hv[j];
                     acc.x = fmaf(x.x, h, acc.x);
                     acc.y = fmaf(x.y, h, acc.y);
@@ -857,7 +877,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
                 for (int u = 0; u < 8; ++u) {
                     const int q = l8 + 8 * u;
                     if (q < nq4) {
-                        const float4 x = Xs4[(size_t)j * nq4 + q], w4 = reinterpret_cast<const float4*>(w_in)[q];
+                        const float4 x = H4m[(size_t)j * nq4 + q], w4 = reinterpret_cast<const float4*>(w_in)[q];
                         part += (x.x * w4.x + x.y * w4.y) + (x.z * w4.z + x.w * w4.w);
                     }
                 }
@@ -982,6 +1002,12 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     unsigned char* Wh = big + A.sz_a;
     unsigned char* Wl = big + A.sz_a + A.sz_opg;
     const float zscale = rs * rsqrtf(c);
+    if (A.hs_w) {   // S's operand from the halo rows staged below it, before Z's operand replaces them
+        float4* h4 = reinterpret_cast<float4*>(big);
+        restage(h4);
+        write_S(Wh, Wl, h4);
+        __syncthreads();
+    }
 #pragma unroll 1
     for (int q8 = 0; q8 < nq; ++q8) {
         float zv[8];
@@ -990,7 +1016,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
         for (int u = 0; u < 8; ++u) zv[u] = (row < P && col0 + 8 * q8 + u < P) ? zv[u] * zscale : 0.f;
         if (row < NP) store8(Zt_h, Zt_l, row, col0 + 8 * q8, NP, zv, true);
     }
-    write_S(Wh, Wl);
+    if (!A.hs_w) write_S(Wh, Wl, Xs4);
     to_mma();
     if (tid == 0) {
         tc_fence_after();
@@ -2397,6 +2423,7 @@ int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 struct FusedLayout {
     int NP, KP, RA, sz_op, sz_opg, sz_a, off_vec, off_xe, off_xh, off_big, off_zf = 0, off_vs = -1, total;
+    int off_hs = -1, off_hs2 = -1, hs_w = 0;
 };
 
 // Ensembles of m >= 128 members do not fit one 128-row MMA tile: they take the dual form.
@@ -2426,7 +2453,20 @@ FusedLayout fused_layout(const letkf_ctx* c) {
         // operands, which are read by then; below them the AR(2) hand-over rows
         L.off_zf = L.sz_a;
         const int epi = L.off_zf + L.RA * (L.KP + 4) * 4;
-        L.total = L.off_big + round_up(std::max(std::max(gram, epi), std::max(ns, tr)), 1024);
+        int big = round_up(std::max(std::max(gram, epi), std::max(ns, tr)), 1024);
+        // the halo anomalies' rows (FP32) in shared memory where they fit: past the Gram operand
+        // for its slopes, past Z's FP32 rows for the mean weights, below the W operand for its
+        // slopes (otherwise those phases read them from the L2-resident scratch)
+        const int hs_bytes = std::max(h.n_h_max, 1) * c->m_pad * 4;
+        const int limit = 227 * 1024 - L.off_big;
+        L.off_hs = round_up(gram, 1024);
+        if (L.off_hs + hs_bytes > limit) L.off_hs = -1;
+        L.off_hs2 = round_up(8192 + L.NP * (L.NP + 4) * 4, 1024);
+        if (L.off_hs2 + hs_bytes > limit) L.off_hs2 = -1;
+        L.hs_w = hs_bytes <= L.sz_a ? 1 : 0;
+        if (L.off_hs >= 0) big = std::max(big, round_up(L.off_hs + hs_bytes, 1024));
+        if (L.off_hs2 >= 0) big = std::max(big, round_up(L.off_hs2 + hs_bytes, 1024));
+        L.total = L.off_big + big;
         return L;
     }
     L.NP = round_up(c->m + 1, 16);
@@ -2620,6 +2660,9 @@ void fill_desc(const FusedFrame& f, const float* V, SysDesc* S) {
     S->sz_a = L.sz_a;
     S->off_zf = L.off_zf;
     S->off_vs = L.off_vs;
+    S->off_hs = L.off_hs;
+    S->off_hs2 = L.off_hs2;
+    S->hs_w = L.hs_w;
     S->cap = c->cap_dev;
     S->cap_dom = c->cap_dom;
 }
