@@ -690,6 +690,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
     const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
     const float inv_cs = 1.f / (c * s_ns);
     const float ns_last = ns_stop(A.ns_last, A.gram_terms, s_scale, A.s_split);
+    const float id_scale = 1.f / s_ns;   // A_s = I / s_ns + K / (c s_ns) by multiplications
     // ---- Z = ((I + K/c)/s)^(-1/2) by the coupled Newton-Schulz iteration (dimension P), from
     //      Y_0 = A_s, Z_0 = I: the first step's P_0 = Z_0 Y_0 is Y_0 itself, so one pass over G
     //      writes Y_0, T_0 = (3I - Y_0)/2, Z_0 and the residual, and the step's two products follow
@@ -703,7 +704,7 @@ __device__ __noinline__ bool analyse_dual(Ctrl* ctl, unsigned char* smem, uint32
             const int j = col0 + 8 * q8 + u;
             const bool in = row < P && j < P;
             const float id = (row == j) ? 1.f : 0.f;
-            yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
+            yv[u] = in ? fmaf(g[u], inv_cs, id * id_scale) : 0.f;
             zv[u] = in ? id : 0.f;
             tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
             if (in) r2_0 += (id - yv[u]) * (id - yv[u]);
@@ -1805,6 +1806,9 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             const float s_ns = s_scale / NS_SCALE;   // the iteration's scale (see NS_SCALE)
             const float inv_cs = 1.f / (c * s_ns);
             const float ns_last = ns_stop(A.ns_last, A.gram_terms, s_scale, A.s_split);
+            // A_s = I / s_ns + G / (c s_ns) by multiplications (two IEEE divisions per element cost
+            // this pass two thirds of its time)
+            const float id_scale = 1.f / s_ns;
             // ---- 3b. coupled Newton-Schulz iteration: P = Z Y, T = (3I - P)/2, Y <- Y T, Z <- T Z,
             //      from Y_0 = A_s, Z_0 = I.  The first step needs no product for P_0 = Y_0 nor for
             //      Z_1 = T_0: one pass over G writes Y_0, T_0 as Z_1 and the residual; Y_1 = Y_0 T_0
@@ -1823,7 +1827,7 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
                         const int j = col0 + 8 * q8 + u;
                         const bool in = row < m && j < m;
                         const float id = (row == j) ? 1.f : 0.f;
-                        yv[u] = in ? (id + g[u] / c) / s_ns : 0.f;
+                        yv[u] = in ? fmaf(g[u], inv_cs, id * id_scale) : 0.f;
                         const float rr = id - yv[u];
                         if (in) r2 += rr * rr;
                         tv[u] = in ? 1.5f * id - 0.5f * yv[u] : 0.f;
