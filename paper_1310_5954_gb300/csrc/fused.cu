@@ -2160,7 +2160,9 @@ __global__ void __launch_bounds__(FT, 1) fused_kernel(const __grid_constant__ Fu
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
-            if (tid == 0) {
+            // the product is issued from warp 1, so that its issue loop (one tcgen05.mma per K step
+            // and term, ~2.7 k cycles) overlaps warp 0's fetch of the next item
+            if (tid == 32) {
                 tc_fence_after();
                 issue_product(tbase + TM_P, Ah, Al, Bh, Bl, NP, NP, A.tr_terms, 1);   // X'_E T
                 mma_commit(&ctl->bar_mma);
