@@ -233,13 +233,14 @@ def _global_roofline(tflops):
             "peak_source": src}
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary of this kernel, or None when the
-    kernel source changed since the counters were taken (the summary records its hash)."""
+def _traffic(kernel, workload, precision):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on this workload and
+    precision (key "kernel:workload:precision"), or None when there is none or the kernel source
+    changed since the counters were taken (the summary records its hash)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path)).get(kernel)
+        rec = json.load(open(path)).get(f"{kernel}:{workload}:{precision}")
         src = os.path.join(ROOT, "paper_1310_5954_gb300", "csrc", rec["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         return rec["dram_bytes_per_launch"] if h == rec["source_sha256"] else None
@@ -247,7 +248,7 @@ def _traffic(kernel):
         return None
 
 
-def roofline(f, prof, sms, sm_max_mhz):
+def roofline(f, prof, sms, sm_max_mhz, workload=None):
     """Roofline of the dominant stage (largest summed CUDA-event time over the profiled steps).
 
     Algorithmic work of one frame (per-unit counts):
@@ -268,7 +269,7 @@ def roofline(f, prof, sms, sm_max_mhz):
         pk = peaks().get("bf16_tflops", 1900.0)
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         return {"kernel": "fused_kernel", "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk, "traffic": _traffic("fused_kernel"), "per_launch_ms": per_launch_ms,
+                "frac": achieved / pk, "traffic": _traffic("fused_kernel", workload, f.precision), "per_launch_ms": per_launch_ms,
                 "work_per_launch_flop": flops,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
     if name == "eigensolve_weights":
@@ -707,7 +708,7 @@ def main():
         tot = float(t.item())
     value = world * K / tot
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    roof = roofline(f, prof, torch.cuda.get_device_properties(dev).multi_processor_count, sm_max)
+    roof = roofline(f, prof, torch.cuda.get_device_properties(dev).multi_processor_count, sm_max, args.workload)
     # end to end through the public API, host buffers
     y_host = torch.as_tensor(y, dtype=f.dtype).pin_memory()
     fe = make_filter(w, args.path, precision, L, Ls, rank)

@@ -185,6 +185,11 @@ WORKLOADS = {
                     ar1_a=0.99, sigma=0.1, tel_diam=16.0, d_over_r0=16.0 / 0.525, L0=25.0, wind=7.5,
                     frame_rate=500.0, n_frames=2000, q=10,
                     layers=((0.5, 7.5, 0.0), (0.17, 12.5, math.pi / 3), (0.33, 15.0, 2 * math.pi / 3))),
+    # The ELT system above with 200 members (the same seed, so the same frames): every domain takes
+    # the observation-space (dual) form of the analysis, as the serving mix's m = 200 systems do.
+    "elt-80x80-m200": _wl(2, name="elt-80x80-m200", n_sub=80, obstruction=0.28, m=200, dom_sub=4, halo=2,
+                          ar1_a=0.995, sigma=0.2, tel_diam=40.0, d_over_r0=40.0, L0=25.0, wind=15.0,
+                          frame_rate=1000.0, n_frames=5000),
     # The same ELT system under a non-stationary schedule (see Workload methods).
     "elt-80x80-nonstationary": _wl(3, name="elt-80x80-nonstationary", n_sub=80, obstruction=0.28,
                                    m=100, dom_sub=4, halo=2, ar1_a=0.995, sigma=0.1, tel_diam=40.0,
