@@ -52,3 +52,25 @@ def test_cpu_baseline_scores_every_frame_of_a_short_run(warmup, steps):
     _, preds_pl, nfr_pl, _ = bench.cpu_baseline("tiny-8x8", y, 600.0, L, Ls, piston="in_loop")
     assert nfr_pl == warmup + steps
     assert np.isfinite(bench.residual_rms(preds_pl, phi, nb))
+
+
+def test_traffic_record_matches_kernel_source_workload_and_precision(tmp_path, monkeypatch):
+    # roofline.traffic comes from the committed ncu record only for the same kernel source (its
+    # hash), workload and precision; anything else reports no traffic rather than a stale figure
+    import hashlib
+    import json
+    bench = _bench()
+    src = tmp_path / "paper_1310_5954_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k.cu").write_text("kernel source")
+    sha = hashlib.sha256(b"kernel source").hexdigest()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"source": "k.cu", "source_sha256": sha, "dram_bytes_per_launch": 1234}
+    (prof / "traffic.json").write_text(json.dumps({"fk:wl:mixed": rec}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic("fk", "wl", "mixed") == 1234
+    assert bench._traffic("fk", "wl", "fp32") is None
+    assert bench._traffic("fk", "other", "mixed") is None
+    (src / "k.cu").write_text("kernel source, changed")
+    assert bench._traffic("fk", "wl", "mixed") is None
