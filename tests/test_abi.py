@@ -203,3 +203,15 @@ def test_domain_offset_outside_the_block_is_refused(lib):
                               precision="fp32", path="fused", dom_offset=off)
         out = ctypes.c_void_p(1234)
         assert lib.letkf_create(ctypes.byref(p), ctypes.byref(out)) == _lib.LETKF_EINVAL
+
+
+@pytest.mark.parametrize("m", [128, 160, 200, 256])
+def test_fused_plan_dual_form_fits_shared_memory(lib, m):
+    # the observation-space form at ELT geometry over its whole ensemble range: operands, the
+    # halo anomalies' rows staged beside them and the epilogue's rows of P3 within one CTA's
+    # 227 KB; its footprint grows with m
+    smem, q, n = _plan(**dict(ELT, m=m))
+    assert (q, n) == (0, 0)
+    assert 0 < smem <= 227 * 1024
+    if m > 128:
+        assert smem >= _plan(**dict(ELT, m=128))[0]
